@@ -1,0 +1,186 @@
+/*
+ * bmmc.h -- C ABI of the GB300 (sm_103a) BMMC permutation library.
+ *
+ * A BMMC (Bit Matrix Multiply Complement) permutation of an array of 2^n
+ * elements moves the element at index x to index y = A x + c, where indices
+ * are read as vectors in F2^n, A is an invertible n x n matrix over F2 and c
+ * is a vector of F2^n (Bouverot-Dupuis & Sheeran, "Efficient GPU
+ * Implementation of Affine Index Permutations on Arrays", Sec. 3).  This
+ * library computes
+ *
+ *        out[A x + c] = in[x]        for every x in [0, 2^n)
+ *
+ * on the GPU, the scatter form the paper's kernels write (Sec. 4.1, Sec. 5.1).
+ *
+ * Conventions used by every entry point:
+ *  - A is passed as n row masks A_rows[0..n-1]; bit j of A_rows[i] is the
+ *    entry a_ij, so row i produces output bit y_i.  Bit 0 is the least
+ *    significant bit of an index.  c is a mask whose bit i is c_i.
+ *  - 1 <= n <= 32.  No mask may have a bit at position >= n set.
+ *  - Elements are opaque blobs of elem_bytes bytes, elem_bytes in {4, 8, 16}.
+ *    Bytes are copied, never interpreted (NaN payloads and -0.0 survive).
+ *  - Device buffers hold 2^n * elem_bytes bytes, contiguous, start on a
+ *    16-byte boundary, and are owned by the caller.  The permutation is never
+ *    in place: in and out must not overlap.
+ *  - Execution is asynchronous on the given stream.  A NULL stream is the
+ *    legacy default stream.  Launch errors are returned synchronously as
+ *    BMMC_ERR_CUDA; faults during execution surface at the caller's next
+ *    synchronisation with the stream.
+ *  - All functions return BMMC_OK (0) or a negative BMMC_ERR_* code, except
+ *    where stated otherwise.
+ */
+#ifndef BMMC_H
+#define BMMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (the same object as cudaStream_t / CUstream). */
+struct CUstream_st;
+typedef struct CUstream_st *bmmc_stream_t;
+
+/* Opaque plan: the validated matrix, its factorisation into passes, and the
+ * launch tables of every pass.  It may also own a device workspace (see
+ * bmmc_execute).  Plans are immutable once created. */
+typedef struct bmmc_plan_s *bmmc_plan;
+
+enum bmmc_status {
+    BMMC_OK = 0,
+    BMMC_ERR_INVALID = -1,     /* n out of range, bits >= n set, NULL pointer */
+    BMMC_ERR_SINGULAR = -2,    /* A is not invertible over F2 (Sec. 3) */
+    BMMC_ERR_UNSUPPORTED = -3, /* elem_bytes not 4, 8 or 16; bad option */
+    BMMC_ERR_ALIAS = -4,       /* in, out (or the workspace) overlap */
+    BMMC_ERR_ALIGN = -5,       /* a device pointer is not 16-byte aligned */
+    BMMC_ERR_OOM = -6,         /* device or host allocation failed */
+    BMMC_ERR_CUDA = -7         /* a CUDA runtime call or launch failed */
+};
+
+/* Planning strategies (bmmc_plan_options.flags). */
+enum bmmc_plan_flags {
+    /* The paper's method: a tiled BMMC (Sec. 5.1) runs as one pass; any other
+     * BMMC is factorised as A = (U R)(R L P) and runs as two tiled passes,
+     * (R L P, 0) first and then (U R, c) (Sec. 5.2). */
+    BMMC_PLAN_PAPER = 0,
+    /* One pass for every BMMC.  Each tile is a coset of the subspace spanned
+     * by the low index bits and the kernel of the high output rows of A, so it
+     * holds whole input segments and whole output segments whatever A is.
+     * This goes beyond the paper, whose tiles are always spanned by unit
+     * vectors; the result is the same permutation. */
+    BMMC_PLAN_SINGLE_PASS = 1
+};
+
+/* Tuning knobs.  Zero in a field selects the library default. */
+typedef struct bmmc_plan_options {
+    uint32_t flags;      /* a bmmc_plan_flags value */
+    int seg_bits;        /* log2 of the elements in one contiguous segment
+                            (the paper's n_tile); must satisfy
+                            2^seg_bits * elem_bytes >= 128 */
+    int cta_tile_log2;   /* log2 of the bytes one thread block moves */
+    int reserved[5];     /* must be zero */
+} bmmc_plan_options;
+
+/*
+ * Create a plan for (A, c) on arrays of 2^n elements of elem_bytes bytes,
+ * with the default options (BMMC_PLAN_PAPER).
+ *
+ * Follows Sec. 3 (definition and invertibility requirement), Sec. 5.1
+ * (tiled test), Sec. 5.2 (factorisation) and Sec. 4.1-4.3 (tile partition).
+ * Host only: touches no GPU and allocates no device memory.
+ *
+ * out      receives the new plan (set to NULL on failure); release it with
+ *          bmmc_plan_destroy.
+ * A_rows   n row masks, read during the call only.
+ * Errors: INVALID, SINGULAR, UNSUPPORTED, OOM.
+ */
+int bmmc_plan_create(bmmc_plan *out, int n, const uint64_t *A_rows, uint64_t c,
+                     size_t elem_bytes);
+
+/* As bmmc_plan_create with explicit options (opts may be NULL). */
+int bmmc_plan_create_ex(bmmc_plan *out, int n, const uint64_t *A_rows,
+                        uint64_t c, size_t elem_bytes,
+                        const bmmc_plan_options *opts);
+
+/* Release a plan and the device workspace it owns.  NULL-safe.  The caller
+ * must make sure no execution that uses the plan's own workspace is still
+ * running. */
+void bmmc_plan_destroy(bmmc_plan p);
+
+/* Number of kernel passes bmmc_execute runs: 1 or 2 (Sec. 5.2).
+ * Returns a negative code for a NULL plan. */
+int bmmc_plan_num_passes(bmmc_plan p);
+
+/* The plan's own matrix A (n row masks into rows_out) and complement c.
+ * Errors: INVALID. */
+int bmmc_plan_matrix(bmmc_plan p, uint64_t *rows_out, uint64_t *c_out);
+
+/* The matrix and complement of pass `pass` (0-based, in execution order).
+ * For a two-pass plan, pass 0 is (R L P, 0) and pass 1 is (U R, c), whose
+ * product is A (Sec. 5.2).  rows_out must hold n masks.
+ * Errors: INVALID. */
+int bmmc_plan_pass_matrix(bmmc_plan p, int pass, uint64_t *rows_out,
+                          uint64_t *c_out);
+
+/* Create the plan of the inverse permutation, (A^{-1}, A^{-1} c), with the
+ * same element size and options.  Applying it to the output of p gives back
+ * the input; it is also the backward pass of p for gradients.  The inverse
+ * follows from Sec. 3's definition and the fusion rule (Sec. 3).
+ * Errors: INVALID, OOM. */
+int bmmc_plan_inverse(bmmc_plan p, bmmc_plan *out);
+
+/* Device workspace bytes bmmc_execute_ws needs: 2^n * elem_bytes for a
+ * two-pass plan, 0 for a one-pass plan.  Returns 0 for a NULL plan. */
+size_t bmmc_plan_workspace_bytes(bmmc_plan p);
+
+/*
+ * Run the permutation: out[A x + c] = in[x] (Sec. 3).
+ *
+ * in, out  device buffers of 2^n * elem_bytes bytes (see conventions).
+ * stream   CUDA stream to run on.
+ *
+ * A two-pass plan needs a workspace of bmmc_plan_workspace_bytes bytes; on
+ * its first two-pass execution the plan allocates one (cudaMalloc) and keeps
+ * it until bmmc_plan_destroy.  Because that workspace is shared, at most one
+ * execution of a given plan may be in flight at a time with this entry
+ * point; use bmmc_execute_ws with distinct workspaces for concurrent
+ * executions of one plan.
+ * Errors: INVALID, ALIAS, ALIGN, OOM, CUDA.
+ */
+int bmmc_execute(bmmc_plan p, const void *in, void *out, bmmc_stream_t stream);
+
+/* As bmmc_execute, with a caller-owned device workspace of at least
+ * bmmc_plan_workspace_bytes(p) bytes (16-byte aligned, overlapping neither
+ * in nor out).  ws may be NULL for a one-pass plan.
+ * Errors: INVALID, ALIAS, ALIGN, CUDA. */
+int bmmc_execute_ws(bmmc_plan p, const void *in, void *out, void *ws,
+                    bmmc_stream_t stream);
+
+/*
+ * Host-side check of a plan's launch tables, with no GPU: walks the index
+ * arithmetic of every pass for up to max_ctas thread blocks per pass (0 =
+ * all of them) and checks that each thread block reads distinct input
+ * elements into distinct shared-memory slots, that each output element it
+ * writes is A' x + c' of the input element x it copies (A', c' being the
+ * pass's matrix), and, when all blocks are walked, that every element is
+ * read and written exactly once.  It moves no data.
+ * Errors: INVALID, or BMMC_ERR_UNSUPPORTED if a check fails.
+ */
+int bmmc_plan_verify(bmmc_plan p, uint64_t max_ctas);
+
+/* Write a one-line JSON description of the plan (passes, segment bits,
+ * tile shape, launch shape, shared-memory bank wavefronts per chunk) into
+ * buf (NUL-terminated, truncated to len).  Returns the full length needed,
+ * or a negative code. */
+int bmmc_plan_describe(bmmc_plan p, char *buf, size_t len);
+
+/* A static, human-readable name for a status code. */
+const char *bmmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BMMC_H */

@@ -26,15 +26,17 @@
 #include <stdint.h>
 #include <string.h>
 
-/* Parity of the set bits of x: the F2 sum of a row-times-vector product. */
+/* Parity of the set bits of x: the F2 sum of a row-times-vector product.
+ * Folding halves with XOR keeps the sum of all bits mod 2 in the low bit. */
 static unsigned parity_u64(uint64_t x)
 {
-    unsigned p = 0;
-    while (x) {
-        p ^= (unsigned)(x & 1u);
-        x >>= 1;
-    }
-    return p;
+    x ^= x >> 32;
+    x ^= x >> 16;
+    x ^= x >> 8;
+    x ^= x >> 4;
+    x ^= x >> 2;
+    x ^= x >> 1;
+    return (unsigned)(x & 1u);
 }
 
 /* y = A x + c (Sec. 3): bit i of y is the parity of (row_i AND x), plus c_i. */

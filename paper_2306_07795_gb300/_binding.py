@@ -1,0 +1,178 @@
+"""ctypes binding of the C ABI in include/bmmc.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  The library
+must be built (``build.build()``); there is no fallback of any kind: if the
+shared library is missing or fails to load, importing the package's GPU entry
+points raises.
+"""
+
+import ctypes
+import json
+import os
+
+from . import build as _build
+
+BMMC_OK = 0
+BMMC_ERR_INVALID = -1
+BMMC_ERR_SINGULAR = -2
+BMMC_ERR_UNSUPPORTED = -3
+BMMC_ERR_ALIAS = -4
+BMMC_ERR_ALIGN = -5
+BMMC_ERR_OOM = -6
+BMMC_ERR_CUDA = -7
+
+BMMC_PLAN_PAPER = 0
+BMMC_PLAN_SINGLE_PASS = 1
+
+# Every entry point declared in include/bmmc.h (checked by the tests).
+EXPORTED = (
+    "bmmc_plan_create", "bmmc_plan_create_ex", "bmmc_plan_destroy",
+    "bmmc_plan_num_passes", "bmmc_plan_matrix", "bmmc_plan_pass_matrix",
+    "bmmc_plan_inverse",
+    "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws",
+    "bmmc_plan_verify", "bmmc_plan_describe", "bmmc_strerror",
+)
+
+
+class BmmcError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = lib().bmmc_strerror(code).decode()
+        super().__init__("%s failed: %s (%d)" % (what, msg, code))
+
+
+class bmmc_plan_options(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("seg_bits", ctypes.c_int),
+                ("cta_tile_log2", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libbmmc.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libbmmc.so is missing: the CUDA library was not built")
+    L = ctypes.CDLL(path)
+    vp, u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
+    sig = {
+        "bmmc_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, u64p,
+                                            ctypes.c_uint64, ctypes.c_size_t]),
+        "bmmc_plan_create_ex": (ctypes.c_int,
+                                [ctypes.POINTER(vp), ctypes.c_int, u64p,
+                                 ctypes.c_uint64, ctypes.c_size_t,
+                                 ctypes.POINTER(bmmc_plan_options)]),
+        "bmmc_plan_destroy": (None, [vp]),
+        "bmmc_plan_num_passes": (ctypes.c_int, [vp]),
+        "bmmc_plan_matrix": (ctypes.c_int, [vp, u64p, u64p]),
+        "bmmc_plan_pass_matrix": (ctypes.c_int, [vp, ctypes.c_int, u64p, u64p]),
+        "bmmc_plan_inverse": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
+        "bmmc_plan_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "bmmc_execute": (ctypes.c_int, [vp, vp, vp, vp]),
+        "bmmc_execute_ws": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bmmc_plan_verify": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "bmmc_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "bmmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code, what):
+    if code != BMMC_OK:
+        raise BmmcError(code, what)
+
+
+def _rows(rows):
+    return (ctypes.c_uint64 * max(1, len(rows)))(*[int(r) for r in rows])
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C names
+# ---------------------------------------------------------------------------
+
+def bmmc_plan_create(n, rows, c, elem_bytes):
+    h = ctypes.c_void_p()
+    _check(lib().bmmc_plan_create(ctypes.byref(h), n, _rows(rows), c, elem_bytes),
+           "bmmc_plan_create")
+    return h
+
+
+def bmmc_plan_create_ex(n, rows, c, elem_bytes, flags=0, seg_bits=0,
+                        cta_tile_log2=0):
+    h = ctypes.c_void_p()
+    o = bmmc_plan_options(flags, seg_bits, cta_tile_log2)
+    _check(lib().bmmc_plan_create_ex(ctypes.byref(h), n, _rows(rows), c,
+                                     elem_bytes, ctypes.byref(o)),
+           "bmmc_plan_create_ex")
+    return h
+
+
+def bmmc_plan_destroy(h):
+    lib().bmmc_plan_destroy(h)
+
+
+def bmmc_plan_num_passes(h):
+    return lib().bmmc_plan_num_passes(h)
+
+
+def bmmc_plan_matrix(h, n):
+    rows = (ctypes.c_uint64 * n)()
+    c = ctypes.c_uint64()
+    _check(lib().bmmc_plan_matrix(h, rows, ctypes.byref(c)), "bmmc_plan_matrix")
+    return [int(r) for r in rows], int(c.value)
+
+
+def bmmc_plan_pass_matrix(h, n, pass_index):
+    rows = (ctypes.c_uint64 * n)()
+    c = ctypes.c_uint64()
+    _check(lib().bmmc_plan_pass_matrix(h, pass_index, rows, ctypes.byref(c)),
+           "bmmc_plan_pass_matrix")
+    return [int(r) for r in rows], int(c.value)
+
+
+def bmmc_plan_inverse(h):
+    out = ctypes.c_void_p()
+    _check(lib().bmmc_plan_inverse(h, ctypes.byref(out)), "bmmc_plan_inverse")
+    return out
+
+
+def bmmc_plan_workspace_bytes(h):
+    return int(lib().bmmc_plan_workspace_bytes(h))
+
+
+def bmmc_execute(h, in_ptr, out_ptr, stream=0):
+    _check(lib().bmmc_execute(h, in_ptr, out_ptr, stream), "bmmc_execute")
+
+
+def bmmc_execute_ws(h, in_ptr, out_ptr, ws_ptr, stream=0):
+    _check(lib().bmmc_execute_ws(h, in_ptr, out_ptr, ws_ptr, stream),
+           "bmmc_execute_ws")
+
+
+def bmmc_plan_verify(h, max_ctas=0):
+    return lib().bmmc_plan_verify(h, max_ctas)
+
+
+def bmmc_plan_describe(h):
+    need = lib().bmmc_plan_describe(h, None, 0)
+    buf = ctypes.create_string_buffer(need + 1)
+    lib().bmmc_plan_describe(h, buf, need + 1)
+    return json.loads(buf.value.decode())
+
+
+def bmmc_strerror(code):
+    return lib().bmmc_strerror(code).decode()

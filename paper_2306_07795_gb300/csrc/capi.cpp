@@ -1,0 +1,319 @@
+// capi.cpp -- the C ABI declared in include/bmmc.h.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "bmmc.h"
+#include "f2.hpp"
+#include "pass_desc.h"
+#include "plan.hpp"
+
+namespace bmmc {
+cudaError_t launch_pass(const PassDesc &d, const void *in, void *out, cudaStream_t s);
+}
+
+using namespace bmmc;
+
+struct bmmc_plan_s {
+    int n = 0;
+    int e_log = 0;
+    uint64_t c = 0;
+    f2::Mat a;
+    PlanOptions opt;
+    int npass = 0;
+    f2::Mat t[2];
+    uint64_t tc[2] = {0, 0};
+    PassDesc desc[2];
+    PassInfo info[2];
+    // Workspace owned by the plan for bmmc_execute (two-pass plans only).
+    std::mutex ws_mu;
+    void *ws = nullptr;
+    int ws_device = -1;
+};
+
+namespace {
+
+int elem_log(size_t e)
+{
+    switch (e) {
+    case 4: return 2;
+    case 8: return 3;
+    case 16: return 4;
+    default: return -1;
+    }
+}
+
+uint64_t array_bytes(const bmmc_plan_s *p) { return (1ull << p->n) << p->e_log; }
+
+bool overlap(const void *a, const void *b, uint64_t bytes)
+{
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
+                size_t elem_bytes, const bmmc_plan_options *opts)
+{
+    if (!out) return BMMC_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || n > kMaxN || !rows) return BMMC_ERR_INVALID;
+    const uint64_t nmask = (n == 64) ? ~0ull : ((1ull << n) - 1);
+    for (int i = 0; i < n; ++i)
+        if (rows[i] & ~nmask) return BMMC_ERR_INVALID;
+    if (c & ~nmask) return BMMC_ERR_INVALID;
+    const int e_log = elem_log(elem_bytes);
+    if (e_log < 0) return BMMC_ERR_UNSUPPORTED;
+
+    PlanOptions opt;
+    if (opts) {
+        for (int r : opts->reserved)
+            if (r) return BMMC_ERR_UNSUPPORTED;
+        if (opts->flags > BMMC_PLAN_SINGLE_PASS) return BMMC_ERR_UNSUPPORTED;
+        opt.flags = opts->flags;
+        opt.seg_bits = opts->seg_bits;
+        opt.cta_tile_log2 = opts->cta_tile_log2;
+        if (opt.seg_bits && (opt.seg_bits < 7 - e_log || opt.seg_bits > 12))
+            return BMMC_ERR_UNSUPPORTED;
+        if (opt.cta_tile_log2 && (opt.cta_tile_log2 < 9 || opt.cta_tile_log2 > 17))
+            return BMMC_ERR_UNSUPPORTED;
+    }
+
+    f2::Mat a;
+    a.n = n;
+    for (int i = 0; i < n; ++i) a.r[i] = rows[i];
+    f2::Mat inv;
+    if (!f2::inverse(a, &inv)) return BMMC_ERR_SINGULAR;
+
+    bmmc_plan_s *p = new (std::nothrow) bmmc_plan_s();
+    if (!p) return BMMC_ERR_OOM;
+    p->n = n;
+    p->e_log = e_log;
+    p->c = c;
+    p->a = a;
+    p->opt = opt;
+
+    // Classification (Sec. 5.1 / 5.2).  Arrays under 1 KiB and single-pass
+    // plans take one pass; otherwise a tiled matrix takes one pass and any
+    // other is factorised into two tiled passes.
+    int k = opt.seg_bits ? opt.seg_bits : default_seg_bits(e_log);
+    if (k > n) k = n;
+    const bool tiny = ((1ull << (n + e_log)) < 1024);
+    if (tiny || opt.flags == BMMC_PLAN_SINGLE_PASS || f2::tiled_columns(a, k)) {
+        p->npass = 1;
+        p->t[0] = a;
+        p->tc[0] = c;
+    } else {
+        f2::Mat t1, t2;
+        if (!f2::tiled_factors(a, &t1, &t2)) {
+            delete p;
+            return BMMC_ERR_SINGULAR;
+        }
+        p->npass = 2;
+        p->t[0] = t2;  // (R L P, 0) first
+        p->tc[0] = 0;
+        p->t[1] = t1;  // then (U R, c)
+        p->tc[1] = c;
+    }
+    for (int i = 0; i < p->npass; ++i) {
+        int rc = derive_pass(p->t[i], p->tc[i], n, e_log, opt, &p->desc[i], &p->info[i]);
+        if (rc) {
+            delete p;
+            return rc;
+        }
+    }
+    *out = p;
+    return BMMC_OK;
+}
+
+int execute_impl(bmmc_plan p, const void *in, void *out, void *ws, cudaStream_t s)
+{
+    const uint64_t bytes = array_bytes(p);
+    if (((uintptr_t)in | (uintptr_t)out) & 15u) return BMMC_ERR_ALIGN;
+    if (overlap(in, out, bytes)) return BMMC_ERR_ALIAS;
+    if (p->npass == 1) {
+        cudaError_t err = launch_pass(p->desc[0], in, out, s);
+        return err == cudaSuccess ? BMMC_OK : BMMC_ERR_CUDA;
+    }
+    if (!ws) return BMMC_ERR_INVALID;
+    if ((uintptr_t)ws & 15u) return BMMC_ERR_ALIGN;
+    if (overlap(ws, in, bytes) || overlap(ws, out, bytes)) return BMMC_ERR_ALIAS;
+    cudaError_t err = launch_pass(p->desc[0], in, ws, s);
+    if (err != cudaSuccess) return BMMC_ERR_CUDA;
+    err = launch_pass(p->desc[1], ws, out, s);
+    return err == cudaSuccess ? BMMC_OK : BMMC_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bmmc_plan_create(bmmc_plan *out, int n, const uint64_t *A_rows, uint64_t c,
+                     size_t elem_bytes)
+{
+    return create_impl(out, n, A_rows, c, elem_bytes, nullptr);
+}
+
+int bmmc_plan_create_ex(bmmc_plan *out, int n, const uint64_t *A_rows, uint64_t c,
+                        size_t elem_bytes, const bmmc_plan_options *opts)
+{
+    return create_impl(out, n, A_rows, c, elem_bytes, opts);
+}
+
+void bmmc_plan_destroy(bmmc_plan p)
+{
+    if (!p) return;
+    if (p->ws) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (p->ws_device >= 0) cudaSetDevice(p->ws_device);
+        cudaFree(p->ws);
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    delete p;
+}
+
+int bmmc_plan_num_passes(bmmc_plan p) { return p ? p->npass : BMMC_ERR_INVALID; }
+
+int bmmc_plan_matrix(bmmc_plan p, uint64_t *rows_out, uint64_t *c_out)
+{
+    if (!p || !rows_out) return BMMC_ERR_INVALID;
+    for (int i = 0; i < p->n; ++i) rows_out[i] = p->a.r[i];
+    if (c_out) *c_out = p->c;
+    return BMMC_OK;
+}
+
+int bmmc_plan_pass_matrix(bmmc_plan p, int pass, uint64_t *rows_out, uint64_t *c_out)
+{
+    if (!p || !rows_out || pass < 0 || pass >= p->npass) return BMMC_ERR_INVALID;
+    for (int i = 0; i < p->n; ++i) rows_out[i] = p->t[pass].r[i];
+    if (c_out) *c_out = p->tc[pass];
+    return BMMC_OK;
+}
+
+int bmmc_plan_inverse(bmmc_plan p, bmmc_plan *out)
+{
+    if (!p || !out) return BMMC_ERR_INVALID;
+    f2::Mat inv;
+    if (!f2::inverse(p->a, &inv)) return BMMC_ERR_INVALID;
+    bmmc_plan_options o;
+    memset(&o, 0, sizeof(o));
+    o.flags = p->opt.flags;
+    o.seg_bits = p->opt.seg_bits;
+    o.cta_tile_log2 = p->opt.cta_tile_log2;
+    return create_impl(out, p->n, inv.r, inv.apply(p->c), (size_t)1 << p->e_log, &o);
+}
+
+size_t bmmc_plan_workspace_bytes(bmmc_plan p)
+{
+    if (!p || p->npass < 2) return 0;
+    return (size_t)array_bytes(p);
+}
+
+int bmmc_execute(bmmc_plan p, const void *in, void *out, bmmc_stream_t stream)
+{
+    if (!p || !in || !out) return BMMC_ERR_INVALID;
+    void *ws = nullptr;
+    if (p->npass == 2) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return BMMC_ERR_CUDA;
+        std::lock_guard<std::mutex> lock(p->ws_mu);
+        if (p->ws && p->ws_device != dev) return BMMC_ERR_INVALID;
+        if (!p->ws) {
+            if (cudaMalloc(&p->ws, (size_t)array_bytes(p)) != cudaSuccess) {
+                p->ws = nullptr;
+                cudaGetLastError();
+                return BMMC_ERR_OOM;
+            }
+            p->ws_device = dev;
+        }
+        ws = p->ws;
+    }
+    return execute_impl(p, in, out, ws, (cudaStream_t)stream);
+}
+
+int bmmc_execute_ws(bmmc_plan p, const void *in, void *out, void *ws, bmmc_stream_t stream)
+{
+    if (!p || !in || !out) return BMMC_ERR_INVALID;
+    return execute_impl(p, in, out, ws, (cudaStream_t)stream);
+}
+
+int bmmc_plan_verify(bmmc_plan p, uint64_t max_ctas)
+{
+    if (!p) return BMMC_ERR_INVALID;
+    for (int i = 0; i < p->npass; ++i) {
+        std::string why;
+        if (verify_pass(p->desc[i], p->t[i], p->tc[i], max_ctas, &why) != 0) {
+            fprintf(stderr, "bmmc_plan_verify: pass %d: %s\n", i, why.c_str());
+            return BMMC_ERR_UNSUPPORTED;
+        }
+    }
+    // The passes compose to the plan's permutation: (T1, c1) o (T0, c0) = (A, c)
+    // by the fusion rule of Sec. 3.
+    f2::Mat prod = p->t[0];
+    uint64_t pc = p->tc[0];
+    for (int i = 1; i < p->npass; ++i) {
+        pc = p->t[i].apply(pc) ^ p->tc[i];
+        prod = f2::mul(p->t[i], prod);
+    }
+    if (!(prod == p->a) || pc != p->c) {
+        fprintf(stderr, "bmmc_plan_verify: passes do not compose to A\n");
+        return BMMC_ERR_UNSUPPORTED;
+    }
+    return BMMC_OK;
+}
+
+int bmmc_plan_describe(bmmc_plan p, char *buf, size_t len)
+{
+    if (!p) return BMMC_ERR_INVALID;
+    std::string s = "{\"n\": " + std::to_string(p->n) +
+                    ", \"elem_bytes\": " + std::to_string(1 << p->e_log) +
+                    ", \"strategy\": \"" +
+                    (p->opt.flags == BMMC_PLAN_SINGLE_PASS ? "single_pass" : "paper") +
+                    "\", \"passes\": [";
+    for (int i = 0; i < p->npass; ++i) {
+        const PassDesc &d = p->desc[i];
+        const PassInfo &f = p->info[i];
+        char tmp[512];
+        snprintf(tmp, sizeof(tmp),
+                 "%s{\"naive\": %u, \"tiled\": %d, \"seg_bits\": %u, \"row_bits\": %u, "
+                 "\"n_over\": %d, \"tiles_per_block_log2\": %u, \"blocks\": %llu, "
+                 "\"threads\": %u, \"loop\": %u, \"smem_bytes\": %u, "
+                 "\"wavefronts_load\": %d, \"ideal_load\": %d, \"wavefronts_store\": %d, "
+                 "\"ideal_store\": %d, \"lanes34\": [%d, %d], \"rot\": %d, "
+                 "\"sigma\": [%u, %u, %u]}",
+                 i ? ", " : "", d.naive, f.tiled, d.k, d.m, f.n_over, d.it,
+                 (unsigned long long)(1ull << d.n_cta), 1u << d.thread_bits, d.loop,
+                 d.smem_bytes, f.wavefronts_load, f.ideal_load, f.wavefronts_store,
+                 f.ideal_store, f.lane3, f.lane4, f.rot, f.sigma[0], f.sigma[1],
+                 f.sigma[2]);
+        s += tmp;
+    }
+    s += "]}";
+    if (buf && len) {
+        size_t cpy = s.size() < len - 1 ? s.size() : len - 1;
+        memcpy(buf, s.data(), cpy);
+        buf[cpy] = 0;
+    }
+    return (int)s.size();
+}
+
+const char *bmmc_strerror(int code)
+{
+    switch (code) {
+    case BMMC_OK: return "ok";
+    case BMMC_ERR_INVALID: return "invalid argument";
+    case BMMC_ERR_SINGULAR: return "matrix is singular over F2";
+    case BMMC_ERR_UNSUPPORTED: return "unsupported element size or option";
+    case BMMC_ERR_ALIAS: return "buffers overlap";
+    case BMMC_ERR_ALIGN: return "device pointer not 16-byte aligned";
+    case BMMC_ERR_OOM: return "out of memory";
+    case BMMC_ERR_CUDA: return "CUDA error";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+// plan.hpp -- host planner: validation, classification, factorisation and
+// per-pass launch tables.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "f2.hpp"
+#include "pass_desc.h"
+
+namespace bmmc {
+
+struct PlanOptions {
+    uint32_t flags = 0;     // 0 = paper (1 or 2 tiled passes), 1 = single pass
+    int seg_bits = 0;       // 0 = default for the element size
+    int cta_tile_log2 = 0;  // 0 = default (16 KiB per thread block)
+};
+
+// Diagnostics of one pass, reported by bmmc_plan_describe.
+struct PassInfo {
+    int tiled = 0;             // Sec. 5.1 tiled with unit-vector rows
+    int n_over = 0;            // overlap bits (k - m)
+    int wavefronts_load = 0;   // shared-memory wavefronts per warp, phase 1
+    int wavefronts_store = 0;  // per warp per output chunk set, phase 2
+    int ideal_load = 0, ideal_store = 0;
+    int lane3 = -1, lane4 = -1, rot = 0;
+    uint32_t sigma[3] = {0, 0, 0};
+};
+
+// Derive the launch tables of one pass out[T x + c] = in[x].
+// Returns 0 or a negative bmmc status.
+int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
+                const PlanOptions &opt, PassDesc *desc, PassInfo *info);
+
+// Walk the tables of a pass on the host (see bmmc_plan_verify).  Returns 0 if
+// every check passes.
+int verify_pass(const PassDesc &d, const f2::Mat &t, uint64_t c,
+                uint64_t max_ctas, std::string *why);
+
+// Default segment bits for an element size: 256-byte segments.
+int default_seg_bits(int e_log);
+
+}  // namespace bmmc

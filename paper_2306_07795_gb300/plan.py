@@ -1,0 +1,109 @@
+"""Plan: a BMMC permutation bound to an array shape, callable on CUDA tensors."""
+
+from . import _binding as B
+
+
+class Plan:
+    """out[A x + c] = in[x] over arrays of 2^n elements of elem_bytes bytes.
+
+    rows: n row masks (bit j of rows[i] is a_ij); c: complement mask.
+    flags: BMMC_PLAN_PAPER (one tiled pass, or two after the UL.P
+    factorisation) or BMMC_PLAN_SINGLE_PASS.
+    """
+
+    def __init__(self, n, rows, c=0, elem_bytes=4, flags=B.BMMC_PLAN_PAPER,
+                 seg_bits=0, cta_tile_log2=0, _handle=None):
+        self.n = int(n)
+        self.rows = [int(r) for r in rows]
+        self.c = int(c)
+        self.elem_bytes = int(elem_bytes)
+        self.flags = flags
+        self.seg_bits = seg_bits
+        self.cta_tile_log2 = cta_tile_log2
+        if _handle is not None:
+            self._h = _handle
+        else:
+            self._h = B.bmmc_plan_create_ex(self.n, self.rows, self.c,
+                                            self.elem_bytes, flags, seg_bits,
+                                            cta_tile_log2)
+        self._inverse = None
+
+    # -- plan queries -------------------------------------------------------
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nbytes(self):
+        return (1 << self.n) * self.elem_bytes
+
+    @property
+    def num_passes(self):
+        return B.bmmc_plan_num_passes(self._h)
+
+    @property
+    def workspace_bytes(self):
+        return B.bmmc_plan_workspace_bytes(self._h)
+
+    def pass_matrices(self):
+        return [B.bmmc_plan_pass_matrix(self._h, self.n, i)
+                for i in range(self.num_passes)]
+
+    def describe(self):
+        return B.bmmc_plan_describe(self._h)
+
+    def verify(self, max_ctas=0):
+        return B.bmmc_plan_verify(self._h, max_ctas)
+
+    def inverse(self):
+        """Plan of (A^{-1}, A^{-1} c), cached."""
+        if self._inverse is None:
+            h = B.bmmc_plan_inverse(self._h)
+            inv_rows, inv_c = B.bmmc_plan_matrix(h, self.n)
+            self._inverse = Plan(self.n, inv_rows, inv_c, self.elem_bytes,
+                                 self.flags, self.seg_bits, self.cta_tile_log2,
+                                 _handle=h)
+        return self._inverse
+
+    # -- execution ----------------------------------------------------------
+    def _check_tensor(self, t, name):
+        if not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor (there is no CPU path)" % name)
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.numel() * t.element_size() != self.nbytes:
+            raise ValueError("%s holds %d bytes, the plan needs %d"
+                             % (name, t.numel() * t.element_size(), self.nbytes))
+
+    def __call__(self, x, out=None, stream=None, workspace=None):
+        """Permute tensor x (any dtype; its bytes are 2^n elements of
+        elem_bytes).  Returns out (allocated like x if not given)."""
+        import torch
+
+        self._check_tensor(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check_tensor(out, "out")
+        dev = x.device
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        with torch.cuda.device(dev):
+            if self.workspace_bytes:
+                if workspace is None:
+                    workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8,
+                                            device=dev)
+                B.bmmc_execute_ws(self._h, x.data_ptr(), out.data_ptr(),
+                                  workspace.data_ptr(), stream.cuda_stream)
+            else:
+                B.bmmc_execute_ws(self._h, x.data_ptr(), out.data_ptr(), None,
+                                  stream.cuda_stream)
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None:
+            try:
+                B.bmmc_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
