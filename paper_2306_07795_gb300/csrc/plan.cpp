@@ -332,11 +332,27 @@ int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
         return (1 << w_log) * wavefronts(dw, gbits);
     };
 
+    // The swizzle only flips chunk bits, so the lanes of a bank group must
+    // already reach every within-chunk word bit on their own; candidates that
+    // do not are tried with the identity swizzle only.
+    auto within_chunk_rank = [&](const Cand &cd) {
+        int lane_oc[5] = {0, 1, 2, cd.l3, cd.l4};
+        uint32_t v[5];
+        for (int b = 0; b < gbits; ++b) {
+            uint32_t p = oc_p[lane_oc[b]];
+            for (int rb = 0; rb < 2; ++rb)
+                if (cd.rot_lane[rb] == b) p ^= lo_p[rb];
+            v[b] = p & ((1u << w_log) - 1);
+        }
+        return rank_u32(v, gbits);
+    };
+
     for (const Cand &cd : cands) {
         Swizzle sw;
         sw.w_log = w_log;
         int tries = 0;
-        const int max_tries = 2 + (line_mask ? 48 : 0);
+        const bool can_reach = within_chunk_rank(cd) == w_log;
+        const int max_tries = can_reach ? 2 + (line_mask ? 48 : 0) : 1;
         for (; tries < max_tries; ++tries) {
             if (tries == 0) {
                 sw.sigma[0] = sw.sigma[1] = sw.sigma[2] = 0;
