@@ -546,7 +546,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(reps=20)
 
     if rank == 0:
         line = {
