@@ -56,7 +56,8 @@ enum bmmc_status {
     BMMC_ERR_ALIAS = -4,       /* in, out (or the workspace) overlap */
     BMMC_ERR_ALIGN = -5,       /* a device pointer is not 16-byte aligned */
     BMMC_ERR_OOM = -6,         /* device or host allocation failed */
-    BMMC_ERR_CUDA = -7         /* a CUDA runtime call or launch failed */
+    BMMC_ERR_CUDA = -7,        /* a CUDA runtime call or launch failed */
+    BMMC_ERR_TOO_LARGE = -8    /* workspace needed exceeds the static scratch */
 };
 
 /* Planning strategies (bmmc_plan_options.flags). */
@@ -157,6 +158,35 @@ int bmmc_execute(bmmc_plan p, const void *in, void *out, bmmc_stream_t stream);
  * Errors: INVALID, ALIAS, ALIGN, CUDA. */
 int bmmc_execute_ws(bmmc_plan p, const void *in, void *out, void *ws,
                     bmmc_stream_t stream);
+
+/*
+ * Run a plan without allocating any device memory.  The paper has no
+ * counterpart; this entry point exists for callers that may not allocate:
+ * code embedded in a host application that owns all device memory through
+ * its own allocator or budget, latency-critical loops where cudaMalloc could
+ * block and synchronise the device, and programs that must fix their peak
+ * device memory in advance.
+ *
+ * A two-pass plan keeps its intermediate array in one file-scope device array
+ * of BMMC_STATIC_SCRATCH_BYTES bytes, reserved on every GPU that loads the
+ * library's device code and held until the process exits.  A one-pass plan
+ * needs no intermediate array and runs exactly as with bmmc_execute_ws.
+ *
+ * in, out, stream: as for bmmc_execute.
+ * The first call on a device looks up the array's device address (a one-time
+ * set-up per device, done with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * leaves its contents behind: nothing in it needs clearing, because the first
+ * pass overwrites all bytes the second pass reads, but two calls whose
+ * executions overlap on the GPU (different streams, not ordered by events)
+ * race on it and give wrong results.  Order such calls.
+ * Errors: INVALID, ALIAS, ALIGN, CUDA, and TOO_LARGE when the plan's
+ * workspace (2^n * elem_bytes) exceeds BMMC_STATIC_SCRATCH_BYTES; no device
+ * memory is allocated or freed in any case.
+ */
+#define BMMC_STATIC_SCRATCH_BYTES (32u << 20)
+int bmmc_execute_static_ws(bmmc_plan p, const void *in, void *out,
+                           bmmc_stream_t stream);
 
 /*
  * Host-side check of a plan's launch tables, with no GPU: walks the index

@@ -14,7 +14,8 @@ There is no CPU path: without the built library and a GPU, execution raises.
 
 from ._binding import (  # noqa: F401
     BMMC_ERR_ALIAS, BMMC_ERR_ALIGN, BMMC_ERR_CUDA, BMMC_ERR_INVALID,
-    BMMC_ERR_OOM, BMMC_ERR_SINGULAR, BMMC_ERR_UNSUPPORTED, BMMC_OK,
+    BMMC_ERR_OOM, BMMC_ERR_SINGULAR, BMMC_ERR_TOO_LARGE, BMMC_ERR_UNSUPPORTED,
+    BMMC_OK, BMMC_STATIC_SCRATCH_BYTES, bmmc_execute_static_ws,
     BMMC_PLAN_PAPER, BMMC_PLAN_SINGLE_PASS, BmmcError, bmmc_execute,
     bmmc_execute_ws, bmmc_plan_create, bmmc_plan_create_ex,
     bmmc_plan_describe, bmmc_plan_destroy, bmmc_plan_inverse, bmmc_plan_matrix,

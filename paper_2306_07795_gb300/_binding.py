@@ -20,6 +20,8 @@ BMMC_ERR_ALIAS = -4
 BMMC_ERR_ALIGN = -5
 BMMC_ERR_OOM = -6
 BMMC_ERR_CUDA = -7
+BMMC_ERR_TOO_LARGE = -8
+BMMC_STATIC_SCRATCH_BYTES = 32 << 20
 
 BMMC_PLAN_PAPER = 0
 BMMC_PLAN_SINGLE_PASS = 1
@@ -30,7 +32,8 @@ EXPORTED = (
     "bmmc_plan_num_passes", "bmmc_plan_matrix", "bmmc_plan_pass_matrix",
     "bmmc_plan_inverse",
     "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws",
-    "bmmc_plan_verify", "bmmc_plan_describe", "bmmc_strerror",
+    "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
+    "bmmc_strerror",
 )
 
 
@@ -79,6 +82,7 @@ def lib():
         "bmmc_plan_workspace_bytes": (ctypes.c_size_t, [vp]),
         "bmmc_execute": (ctypes.c_int, [vp, vp, vp, vp]),
         "bmmc_execute_ws": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bmmc_execute_static_ws": (ctypes.c_int, [vp, vp, vp, vp]),
         "bmmc_plan_verify": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "bmmc_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -161,6 +165,11 @@ def bmmc_execute(h, in_ptr, out_ptr, stream=0):
 def bmmc_execute_ws(h, in_ptr, out_ptr, ws_ptr, stream=0):
     _check(lib().bmmc_execute_ws(h, in_ptr, out_ptr, ws_ptr, stream),
            "bmmc_execute_ws")
+
+
+def bmmc_execute_static_ws(h, in_ptr, out_ptr, stream=0):
+    _check(lib().bmmc_execute_static_ws(h, in_ptr, out_ptr, stream),
+           "bmmc_execute_static_ws")
 
 
 def bmmc_plan_verify(h, max_ctas=0):
