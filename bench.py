@@ -39,7 +39,7 @@ METRIC = ("effective GB/s (2·N·bytes/s) vs GB300 HBM peak & D2D copy; "
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "bmmc_tiled_pass_traffic.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2306_07795_gb300", "csrc", f)
-                  for f in ("kernels.cu", "pass_desc.h", "plan.cpp")]
+                  for f in ("kernels.cu", "tile_body.cuh", "pass_desc.h", "plan.cpp")]
 
 
 def parse_args():
@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -87,22 +91,29 @@ def barrier(world):
         dist.barrier()
 
 
+def _reduce_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def allreduce_max(world, value):
+    """Max over ranks (the slowest rank's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def allreduce_sum(world, value):
+    """Sum over ranks (the bytes all replicas moved)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
@@ -346,6 +357,209 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
+# Batched, differentiable and served forms (reported beside the headline)
+# ---------------------------------------------------------------------------
+
+def _percentile(values, q):
+    v = sorted(values)
+    k = (len(v) - 1) * q
+    lo = int(k)
+    hi = min(lo + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)
+
+
+def bench_batched(dev, stream, count=4096, seed=7, replays=20, warmup=3):
+    """4096 int32 arrays, n uniform in 10..24, each with its own dense BMMC:
+    one batch (persistent launches, tile options chosen by the autotuner)
+    captured in a CUDA graph, against one plain launch per array."""
+    import torch
+    import paper_2306_07795_gb300 as bm
+    from paper_2306_07795_gb300.autotune import tune_batch
+    from paper_2306_07795_gb300.batch import Batch
+    import workloads as wl
+
+    ns = wl.batched_sizes(count=count, lo=10, hi=24, seed=seed)
+    mats = [wl.dense_bmmc(n, seed * 100003 + i, lib_invertible(n)) for i, n in enumerate(ns)]
+    sizes = [(1 << n) * 4 for n in ns]
+    offs, total = [], 0
+    for s in sizes:
+        offs.append(total)
+        total += (s + 255) // 256 * 256
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    xin = torch.randint(-2**31, 2**31 - 1, (total // 4,), dtype=torch.int32, device=dev,
+                        generator=gen)
+    xout = torch.empty_like(xin)
+    ins = [xin[o // 4:(o + s) // 4] for o, s in zip(offs, sizes)]
+    outs = [xout[o // 4:(o + s) // 4] for o, s in zip(offs, sizes)]
+    moved = sum(2 * s for s in sizes)
+
+    def plans_for(flags, seg, tile):
+        return [bm.Plan(n, rows, c, 4, flags=flags, seg_bits=seg, cta_tile_log2=tile)
+                for n, (rows, c) in zip(ns, mats)]
+
+    def time_graph(batch):
+        graph = batch.capture()
+        for _ in range(warmup):
+            graph.replay()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(replays)]
+        s = torch.cuda.current_stream(dev)
+        for a, b in evs:
+            a.record(s)
+            graph.replay()
+            b.record(s)
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        del graph
+        return ms
+
+    out = {"arrays": count, "elem_bytes": 4, "bytes_moved_per_replay": moved,
+           "n_range": [10, 24]}
+    # autotuner: tile options for the whole batch, paper strategy
+    best, trials = tune_batch(lambda seg, tile: Batch(plans_for(bm.BMMC_PLAN_PAPER, seg, tile),
+                                                      ins, outs), dev)
+    out["autotune"] = {"chosen": {"seg_bits": best[0], "cta_tile_log2": best[1]},
+                       "trials": trials}
+    plans = plans_for(bm.BMMC_PLAN_PAPER, *best)
+    batch = Batch(plans, ins, outs)
+    ms = time_graph(batch)
+    med = statistics.median(ms)
+    out["graph"] = {"launches_per_replay": batch.num_launches,
+                    "gbs": round(moved / (med / 1e3) / 1e9, 1),
+                    "replay_ms_p50": round(_percentile(ms, 0.5), 3),
+                    "replay_ms_p99": round(_percentile(ms, 0.99), 3)}
+    ws_need = batch.workspace.numel() if batch.workspace is not None else 0
+    del batch
+    # plain: one bmmc_execute per array, in order, on one stream
+    ws = torch.empty(max(p.workspace_bytes for p in plans) or 16, dtype=torch.uint8,
+                     device=dev)
+    for p, x, y in zip(plans, ins, outs):
+        p(x, out=y, stream=stream, workspace=ws)
+    plain_ms = []
+    for _ in range(3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for p, x, y in zip(plans, ins, outs):
+            p(x, out=y, stream=stream, workspace=ws)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms.append(a.elapsed_time(b))
+    pm = statistics.median(plain_ms)
+    out["plain_launches"] = {"launches": sum(p.num_passes for p in plans),
+                             "gbs": round(moved / (pm / 1e3) / 1e9, 1),
+                             "ms": round(pm, 3)}
+    out["speedup_vs_plain"] = round(pm / med, 3)
+    out["workspace_bytes"] = ws_need
+    del ws
+    # single-pass strategy (beyond the paper): one launch, no workspace
+    sp = Batch(plans_for(bm.BMMC_PLAN_SINGLE_PASS, *best), ins, outs)
+    ms = time_graph(sp)
+    med1 = statistics.median(ms)
+    out["graph_single_pass"] = {"launches_per_replay": sp.num_launches,
+                                "gbs": round(moved / (med1 / 1e3) / 1e9, 1),
+                                "replay_ms_p50": round(_percentile(ms, 0.5), 3),
+                                "replay_ms_p99": round(_percentile(ms, 0.99), 3)}
+    del sp, xin, xout, ins, outs
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_autograd(dev, iters=20):
+    """[64, 2^20] fp32 through the differentiable permutation: forward and
+    backward (the inverse BMMC) per iteration, against a D2D copy."""
+    import torch
+    import paper_2306_07795_gb300 as bm
+    from paper_2306_07795_gb300.autograd import bmmc_permute
+    import workloads as wl
+
+    n = 20
+    rows, c = wl.dense_bmmc(n, 3, lib_invertible(n))
+    out = {"shape": [64, 1 << n], "dtype": "float32"}
+    gen = torch.Generator(device=dev).manual_seed(3)
+    x = torch.randn(64, 1 << n, device=dev, generator=gen).requires_grad_(True)
+    w = torch.randn(64, 1 << n, device=dev, generator=gen)
+    nbytes = x.numel() * 4
+    for name, flags in (("paper", bm.BMMC_PLAN_PAPER), ("single_pass", bm.BMMC_PLAN_SINGLE_PASS)):
+        plan = bm.Plan(n, rows, c, 4, flags=flags)
+        for _ in range(3):
+            x.grad = None
+            bmmc_permute(x, plan).backward(w)
+        s = torch.cuda.current_stream(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(s)
+        for _ in range(iters):
+            x.grad = None
+            bmmc_permute(x, plan).backward(w)
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / iters
+        out[name] = {"fwd_bwd_ms": round(ms, 4),
+                     "gbs": round(2 * 2 * nbytes / (ms / 1e3) / 1e9, 1)}
+    y = torch.empty_like(w)
+    y.copy_(w)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(iters):
+        y.copy_(w)
+    b.record()
+    torch.cuda.synchronize(dev)
+    d2d = a.elapsed_time(b) / iters
+    out["two_d2d_copies_ms"] = round(2 * d2d, 4)
+    for name in ("paper", "single_pass"):
+        out[name]["frac_of_2x_d2d"] = round(2 * d2d / out[name]["fwd_bwd_ms"], 4)
+    return out
+
+
+def bench_serving(dev, seconds=10.0, rate=2000.0, seed=11, budget=40 * 10**9, streams=4):
+    """Poisson request stream; continuous-admission server vs a plain loop."""
+    import torch
+    from paper_2306_07795_gb300 import serving
+    import workloads as wl
+
+    specs = wl.serving_requests(rate=rate, seconds=seconds, seed=seed)
+    mats = []
+    for s in specs:
+        if s["kind"] == "bp":
+            mats.append((wl.random_bp(s["n"], s["seed"]), 0))
+        else:
+            mats.append(wl.dense_bmmc(s["n"], s["seed"], lib_invertible(s["n"])))
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    pool = torch.randint(-2**31, 2**31 - 1, ((1 << 27) * 8 // 4,), dtype=torch.int32,
+                         device=dev, generator=gen)
+
+    def requests():
+        out = []
+        for i, (s, (rows, c)) in enumerate(zip(specs, mats)):
+            x = pool[: (1 << s["n"]) * s["e"] // 4]
+            out.append(serving.Request(i, s["arrival"], s["n"], s["e"], rows, c, x))
+        return out
+
+    res = {"requests": len(specs), "rate_per_s": rate, "seconds": seconds,
+           "budget_bytes": budget, "streams": streams}
+    srv = serving.Server(dev, budget_bytes=budget, streams=streams)
+    done, makespan = srv.run(requests())
+    res["server"] = serving.summarize(done, makespan)
+    res["server"]["stats"] = dict(srv.stats)
+    del srv, done
+    torch.cuda.empty_cache()
+    done, makespan = serving.serve_plain(requests(), dev)
+    res["plain"] = serving.summarize(done, makespan)
+    del done, pool
+    torch.cuda.empty_cache()
+    for key in ("server", "plain"):
+        for f in ("throughput_req_s", "effective_gbs", "p50_ms", "p99_ms", "mean_ms",
+                  "makespan_s"):
+            res[key][f] = round(res[key][f], 4)
+    res["p99_ratio_plain_over_server"] = round(res["plain"]["p99_ms"] / res["server"]["p99_ms"], 3)
+    return res
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 
@@ -518,23 +732,53 @@ def main():
             host[e] = (hin, hout)
         torch.cuda.synchronize(dev)
 
+        # Two device buffer sets per element size and three streams: the H2D
+        # copy of permutation i+1, the kernels of permutation i and the D2H
+        # copy of permutation i-1 run at once (the host link is full duplex).
+        sets = {e: [bufs[e], tuple(torch.empty_like(t) for t in bufs[e])] for e in elems}
+        s_in = torch.cuda.Stream(device=dev)
+        s_run = torch.cuda.Stream(device=dev)
+        s_out = torch.cuda.Stream(device=dev)
+        done_run = {}   # (e, set) -> event: kernels finished reading x / writing y
+        done_out = {}   # (e, set) -> event: D2H finished reading y
+
         def e2e_step():
             for i, (cls, e, rows, c) in enumerate(items):
-                x, y, ws = bufs[e]
+                k = (e, i & 1)
+                x, y, ws = sets[e][i & 1]
                 hin, hout = host[e]
-                x.copy_(hin, non_blocking=True)
-                plans[i](x, out=y, stream=stream, workspace=ws)
-                hout.copy_(y, non_blocking=True)
+                if k in done_run:
+                    s_in.wait_event(done_run[k])
+                with torch.cuda.stream(s_in):
+                    x.copy_(hin, non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+                s_run.wait_event(ev_in)
+                if k in done_out:
+                    s_run.wait_event(done_out[k])
+                plans[i](x, out=y, stream=s_run, workspace=ws)
+                ev_run = torch.cuda.Event()
+                ev_run.record(s_run)
+                done_run[k] = ev_run
+                s_out.wait_event(ev_run)
+                with torch.cuda.stream(s_out):
+                    hout.copy_(y, non_blocking=True)
+                ev_out = torch.cuda.Event()
+                ev_out.record(s_out)
+                done_out[k] = ev_out
         e2e_step()
         torch.cuda.synchronize(dev)
         barrier(world)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record(s_in)
         for _ in range(args.e2e_steps):
             e2e_step()
-        b.record(stream)
+        s_out.wait_stream(s_in)
+        s_out.wait_stream(s_run)
+        b.record(s_out)
         torch.cuda.synchronize(dev)
+        del sets
         barrier(world)
         ms = allreduce_max(world, a.elapsed_time(b))
         e2e_bytes = allreduce_sum(world, float(bytes_per_step * args.e2e_steps))
@@ -543,6 +787,15 @@ def main():
                "h2d_bytes_per_step": hbytes, "d2h_bytes_per_step": hbytes,
                "steps": args.e2e_steps, "warmup": 1}
         del host
+
+    del bufs
+    torch.cuda.empty_cache()
+    if not args.no_autograd:
+        extras["autograd"] = bench_autograd(dev)
+    if not args.no_batched:
+        extras["batched"] = bench_batched(dev, stream)
+    if not args.no_serving:
+        extras["serving"] = bench_serving(dev, seconds=args.serving_seconds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

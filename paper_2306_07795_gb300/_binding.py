@@ -34,6 +34,10 @@ EXPORTED = (
     "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws",
     "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
     "bmmc_strerror",
+    # include/bmmc_batch.h
+    "bmmc_batch_workspace_bytes", "bmmc_batch_table_bytes", "bmmc_batch_create",
+    "bmmc_batch_execute",
+    "bmmc_batch_num_launches", "bmmc_batch_describe", "bmmc_batch_destroy",
 )
 
 
@@ -67,6 +71,7 @@ def lib():
         raise RuntimeError("libbmmc.so is missing: the CUDA library was not built")
     L = ctypes.CDLL(path)
     vp, u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
+    vpp = ctypes.POINTER(ctypes.c_void_p)
     sig = {
         "bmmc_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, u64p,
                                             ctypes.c_uint64, ctypes.c_size_t]),
@@ -86,6 +91,14 @@ def lib():
         "bmmc_plan_verify": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "bmmc_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "bmmc_batch_workspace_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
+        "bmmc_batch_table_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
+        "bmmc_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), vpp, ctypes.c_int,
+                                             vpp, vpp, vp, vp, vp]),
+        "bmmc_batch_execute": (ctypes.c_int, [vp, vp]),
+        "bmmc_batch_num_launches": (ctypes.c_int, [vp]),
+        "bmmc_batch_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "bmmc_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -185,3 +198,52 @@ def bmmc_plan_describe(h):
 
 def bmmc_strerror(code):
     return lib().bmmc_strerror(code).decode()
+
+
+# ---------------------------------------------------------------------------
+# include/bmmc_batch.h
+# ---------------------------------------------------------------------------
+
+def _ptr_array(values):
+    arr = (ctypes.c_void_p * max(1, len(values)))()
+    for i, v in enumerate(values):
+        arr[i] = v.value if isinstance(v, ctypes.c_void_p) else v
+    return arr
+
+
+def bmmc_batch_workspace_bytes(plan_handles):
+    return int(lib().bmmc_batch_workspace_bytes(_ptr_array(plan_handles),
+                                                len(plan_handles)))
+
+
+def bmmc_batch_table_bytes(plan_handles):
+    return int(lib().bmmc_batch_table_bytes(_ptr_array(plan_handles),
+                                            len(plan_handles)))
+
+
+def bmmc_batch_create(plan_handles, in_ptrs, out_ptrs, ws_ptr, table_ptr, stream=0):
+    h = ctypes.c_void_p()
+    _check(lib().bmmc_batch_create(ctypes.byref(h), _ptr_array(plan_handles),
+                                   len(plan_handles), _ptr_array(in_ptrs),
+                                   _ptr_array(out_ptrs), ws_ptr, table_ptr, stream),
+           "bmmc_batch_create")
+    return h
+
+
+def bmmc_batch_execute(h, stream=0):
+    _check(lib().bmmc_batch_execute(h, stream), "bmmc_batch_execute")
+
+
+def bmmc_batch_num_launches(h):
+    return lib().bmmc_batch_num_launches(h)
+
+
+def bmmc_batch_describe(h):
+    need = lib().bmmc_batch_describe(h, None, 0)
+    buf = ctypes.create_string_buffer(need + 1)
+    lib().bmmc_batch_describe(h, buf, need + 1)
+    return json.loads(buf.value.decode())
+
+
+def bmmc_batch_destroy(h):
+    lib().bmmc_batch_destroy(h)

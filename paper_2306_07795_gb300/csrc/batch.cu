@@ -1,0 +1,370 @@
+// batch.cu -- many BMMC permutations of different sizes in one persistent
+// launch per phase.
+//
+// A batch binds plans[i] to (ins[i], outs[i]).  Its work is the list of
+// thread-block items of every pass: phase 1 holds the first pass of every
+// plan (in -> out for one-pass plans, in -> workspace slice for two-pass
+// plans), phase 2 the second pass of the two-pass plans (workspace -> out,
+// Sec. 5.2).  Each phase is one persistent kernel per element size present:
+// a grid of (SMs x resident blocks) thread blocks, each walking a contiguous
+// range of items, so that small arrays (the paper notes that arrays under
+// 2^20 elements cannot fill a GPU, Sec. 6) share the machine with large ones
+// instead of each needing its own launch.  A block reloads a pass's tables
+// into shared memory only when its range crosses into the next array.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bmmc.h"
+#include "bmmc_batch.h"
+#include "plan_internal.hpp"
+#include "tile_body.cuh"
+
+using namespace bmmc;
+
+namespace {
+
+// One (array, pass) of a phase.
+struct BatchEntry {
+    const uint8_t *src;
+    uint8_t *dst;
+    uint64_t first_item;  // items of the phase before this entry
+    uint32_t desc;        // index of the pass's tables in the desc array
+    uint32_t pad;
+};
+static_assert(sizeof(BatchEntry) == 32, "BatchEntry layout");
+
+// Pass tables are stored, and staged in shared memory, in 128-byte slots.
+constexpr uint32_t kDescSlot = (uint32_t)((sizeof(PassDesc) + 127) & ~(size_t)127);
+constexpr uint32_t kThreads = 256;
+
+template <int E_LOG>
+__global__ void __launch_bounds__(kThreads)
+    bmmc_batch_pass(const BatchEntry *__restrict__ ent, uint32_t count, uint64_t total,
+                    const uint8_t *__restrict__ descs)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const PassDesc &sd = *reinterpret_cast<const PassDesc *>(smem);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem) + kDescSlot;
+
+    const uint64_t begin = total * blockIdx.x / gridDim.x;
+    const uint64_t end = total * (blockIdx.x + 1) / gridDim.x;
+    if (begin >= end) return;
+    // last entry whose first item is <= begin
+    uint32_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (ent[mid].first_item <= begin) lo = mid;
+        else hi = mid - 1;
+    }
+    uint32_t a = lo;
+    uint32_t loaded = 0xffffffffu;
+    for (uint64_t item = begin; item < end; ++item) {
+        while (a + 1 < count && ent[a + 1].first_item <= item) ++a;
+        const BatchEntry en = ent[a];
+        if (en.desc != loaded) {
+            __syncthreads();  // every thread is done with the previous tables
+            const uint4 *src = reinterpret_cast<const uint4 *>(descs + (size_t)en.desc * kDescSlot);
+            uint4 *dst = reinterpret_cast<uint4 *>(smem);
+            for (uint32_t w = threadIdx.x; w < kDescSlot / 16; w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            loaded = en.desc;
+        }
+        if (sd.naive) {
+            dev::run_naive<E_LOG>(sd, en.src, en.dst);
+        } else {
+            const bool active = threadIdx.x < (1u << sd.thread_bits);
+            dev::run_tile<E_LOG>(sd, (uint32_t)(item - en.first_item), en.src, en.dst, sbase,
+                                 active);
+        }
+        __syncthreads();  // the tile buffer is reused by the next item
+    }
+}
+
+struct Group {
+    int e_log = 0;
+    int phase = 0;
+    uint32_t count = 0;
+    uint64_t total = 0;
+    size_t entry_offset = 0;  // byte offset of its entries in the device block
+    uint32_t smem = 0;
+    uint32_t grid = 0;
+    uint32_t arrays = 0;
+};
+
+template <int E_LOG>
+cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
+{
+    const BatchEntry *ent = reinterpret_cast<const BatchEntry *>(dmem + g.entry_offset);
+    bmmc_batch_pass<E_LOG><<<g.grid, kThreads, g.smem, s>>>(ent, g.count, g.total, dmem);
+    return cudaGetLastError();
+}
+
+template <int E_LOG>
+cudaError_t prepare_group(Group *g, int sms)
+{
+    cudaError_t err = cudaFuncSetAttribute(bmmc_batch_pass<E_LOG>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)g->smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bmmc_batch_pass<E_LOG>,
+                                                        kThreads, g->smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (uint64_t)sms * (uint64_t)per_sm;
+    if (grid > g->total) grid = g->total;
+    g->grid = (uint32_t)grid;
+    return cudaSuccess;
+}
+
+uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+struct Range {
+    uintptr_t lo, hi;
+    bool writable;
+};
+
+bool ranges_conflict(std::vector<Range> r)
+{
+    std::sort(r.begin(), r.end(), [](const Range &a, const Range &b) { return a.lo < b.lo; });
+    // any overlap involving a writable range is a conflict; read-only ranges
+    // may overlap each other (several plans may read one input)
+    uintptr_t max_hi_w = 0, max_hi_any = 0;
+    for (const Range &x : r) {
+        if (x.lo < max_hi_w) return true;                 // overlaps an earlier writable
+        if (x.writable && x.lo < max_hi_any) return true;  // writable overlaps anything
+        if (x.writable) max_hi_w = std::max(max_hi_w, x.hi);
+        max_hi_any = std::max(max_hi_any, x.hi);
+    }
+    return false;
+}
+
+}  // namespace
+
+struct bmmc_batch_s {
+    int device = -1;
+    uint8_t *dmem = nullptr;  // caller-owned table memory
+    std::vector<Group> groups;
+    uint64_t bytes_moved = 0;
+};
+
+namespace {
+
+// Bytes of the device tables of a batch: one 128-byte slot per pass, then
+// one BatchEntry per (array, pass).
+size_t table_bytes(const bmmc_plan *plans, int count)
+{
+    size_t passes = 0;
+    for (int i = 0; i < count; ++i)
+        if (plans[i]) passes += (size_t)plans[i]->npass;
+    return passes * kDescSlot + passes * sizeof(BatchEntry);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bmmc_batch_workspace_bytes(const bmmc_plan *plans, int count)
+{
+    if (!plans || count <= 0) return 0;
+    uint64_t total = 0;
+    for (int i = 0; i < count; ++i)
+        if (plans[i] && plans[i]->npass == 2) total = round_up(total, 256) + plans[i]->bytes();
+    return (size_t)total;
+}
+
+size_t bmmc_batch_table_bytes(const bmmc_plan *plans, int count)
+{
+    if (!plans || count <= 0) return 0;
+    return table_bytes(plans, count);
+}
+
+int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
+                      const void *const *ins, void *const *outs, void *ws, void *table,
+                      bmmc_stream_t stream)
+{
+    if (!out) return BMMC_ERR_INVALID;
+    *out = nullptr;
+    if (!plans || !ins || !outs || count <= 0 || !table) return BMMC_ERR_INVALID;
+    if ((uintptr_t)table & 15u) return BMMC_ERR_ALIGN;
+    const size_t ws_need = bmmc_batch_workspace_bytes(plans, count);
+    if (ws_need && !ws) return BMMC_ERR_INVALID;
+    if ((uintptr_t)ws & 15u) return BMMC_ERR_ALIGN;
+
+    // Workspace slices and overlap checks.
+    std::vector<uint8_t *> slice(count, nullptr);
+    std::vector<Range> ranges;
+    ranges.reserve(3 * (size_t)count);
+    uint64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        const bmmc_plan p = plans[i];
+        if (!p || !ins[i] || !outs[i]) return BMMC_ERR_INVALID;
+        if (((uintptr_t)ins[i] | (uintptr_t)outs[i]) & 15u) return BMMC_ERR_ALIGN;
+        const uint64_t b = p->bytes();
+        ranges.push_back({(uintptr_t)ins[i], (uintptr_t)ins[i] + b, false});
+        ranges.push_back({(uintptr_t)outs[i], (uintptr_t)outs[i] + b, true});
+        if (p->npass == 2) {
+            off = round_up(off, 256);
+            slice[i] = (uint8_t *)ws + off;
+            ranges.push_back({(uintptr_t)slice[i], (uintptr_t)slice[i] + b, true});
+            off += b;
+        }
+    }
+    if (ranges_conflict(ranges)) return BMMC_ERR_ALIAS;
+
+    // Pass tables: one slot per (plan, pass).
+    std::vector<uint32_t> desc0(count), desc1(count);
+    uint32_t ndesc = 0;
+    for (int i = 0; i < count; ++i) {
+        desc0[i] = ndesc++;
+        if (plans[i]->npass == 2) desc1[i] = ndesc++;
+    }
+    // Groups in launch order: phase 1 then phase 2, element sizes 4, 8, 16.
+    std::vector<Group> groups;
+    std::vector<BatchEntry> entries;
+    uint64_t moved = 0;
+    for (int phase = 0; phase < 2; ++phase) {
+        for (int e_log = 2; e_log <= 4; ++e_log) {
+            Group g;
+            g.e_log = e_log;
+            g.phase = phase;
+            g.entry_offset = entries.size() * sizeof(BatchEntry);
+            uint32_t max_smem = 0;
+            for (int i = 0; i < count; ++i) {
+                const bmmc_plan p = plans[i];
+                if (p->e_log != e_log || phase >= p->npass) continue;
+                const PassDesc &d = p->desc[phase];
+                BatchEntry en;
+                memset(&en, 0, sizeof(en));
+                if (p->npass == 1) {
+                    en.src = (const uint8_t *)ins[i];
+                    en.dst = (uint8_t *)outs[i];
+                } else if (phase == 0) {
+                    en.src = (const uint8_t *)ins[i];
+                    en.dst = slice[i];
+                } else {
+                    en.src = slice[i];
+                    en.dst = (uint8_t *)outs[i];
+                }
+                en.first_item = g.total;
+                en.desc = phase == 0 ? desc0[i] : desc1[i];
+                entries.push_back(en);
+                g.total += d.naive ? 1ull : (1ull << d.n_cta);
+                g.count += 1;
+                if (!d.naive) max_smem = std::max(max_smem, d.smem_bytes);
+                moved += 2 * p->bytes();
+            }
+            if (g.count == 0) {
+                entries.resize(g.entry_offset / sizeof(BatchEntry));
+                continue;
+            }
+            g.arrays = g.count;
+            g.smem = kDescSlot + max_smem;
+            groups.push_back(g);
+        }
+    }
+
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BMMC_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return BMMC_ERR_CUDA;
+    for (Group &g : groups) {
+        cudaError_t err = cudaSuccess;
+        switch (g.e_log) {
+        case 2: err = prepare_group<2>(&g, sms); break;
+        case 3: err = prepare_group<3>(&g, sms); break;
+        default: err = prepare_group<4>(&g, sms); break;
+        }
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            return BMMC_ERR_CUDA;
+        }
+    }
+
+    // One device block: pass tables, then the entries of every group.
+    const size_t desc_bytes = (size_t)ndesc * kDescSlot;
+    const size_t ent_bytes = entries.size() * sizeof(BatchEntry);
+    std::vector<uint8_t> host(desc_bytes + ent_bytes, 0);
+    for (int i = 0; i < count; ++i) {
+        memcpy(host.data() + (size_t)desc0[i] * kDescSlot, &plans[i]->desc[0], sizeof(PassDesc));
+        if (plans[i]->npass == 2)
+            memcpy(host.data() + (size_t)desc1[i] * kDescSlot, &plans[i]->desc[1],
+                   sizeof(PassDesc));
+    }
+    memcpy(host.data() + desc_bytes, entries.data(), ent_bytes);
+    for (Group &g : groups) g.entry_offset += desc_bytes;
+
+    bmmc_batch_s *b = new (std::nothrow) bmmc_batch_s();
+    if (!b) return BMMC_ERR_OOM;
+    b->dmem = (uint8_t *)table;
+    // From pageable memory the copy is staged before the call returns, so the
+    // host vector may go; the device side is ordered on `stream`.
+    if (cudaMemcpyAsync(b->dmem, host.data(), host.size(), cudaMemcpyHostToDevice,
+                        (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return BMMC_ERR_CUDA;
+    }
+    b->device = dev;
+    b->groups = groups;
+    b->bytes_moved = moved;
+    *out = b;
+    return BMMC_OK;
+}
+
+int bmmc_batch_execute(bmmc_batch b, bmmc_stream_t stream)
+{
+    if (!b) return BMMC_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return BMMC_ERR_INVALID;
+    for (const Group &g : b->groups) {
+        cudaError_t err;
+        switch (g.e_log) {
+        case 2: err = launch_group<2>(g, b->dmem, (cudaStream_t)stream); break;
+        case 3: err = launch_group<3>(g, b->dmem, (cudaStream_t)stream); break;
+        default: err = launch_group<4>(g, b->dmem, (cudaStream_t)stream); break;
+        }
+        if (err != cudaSuccess) return BMMC_ERR_CUDA;
+    }
+    return BMMC_OK;
+}
+
+int bmmc_batch_num_launches(bmmc_batch b) { return b ? (int)b->groups.size() : BMMC_ERR_INVALID; }
+
+int bmmc_batch_describe(bmmc_batch b, char *buf, size_t len)
+{
+    if (!b) return BMMC_ERR_INVALID;
+    std::string s = "{\"launches\": [";
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+        const Group &g = b->groups[i];
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp),
+                 "%s{\"phase\": %d, \"elem_bytes\": %d, \"arrays\": %u, \"items\": %llu, "
+                 "\"grid\": %u, \"threads\": %u, \"smem_bytes\": %u}",
+                 i ? ", " : "", g.phase + 1, 1 << g.e_log, g.arrays,
+                 (unsigned long long)g.total, g.grid, kThreads, g.smem);
+        s += tmp;
+    }
+    char tail[64];
+    snprintf(tail, sizeof(tail), "], \"bytes_moved\": %llu}", (unsigned long long)b->bytes_moved);
+    s += tail;
+    if (buf && len) {
+        size_t cpy = s.size() < len - 1 ? s.size() : len - 1;
+        memcpy(buf, s.data(), cpy);
+        buf[cpy] = 0;
+    }
+    return (int)s.size();
+}
+
+void bmmc_batch_destroy(bmmc_batch b)
+{
+    delete b;  // the table memory belongs to the caller
+}
+
+}  // extern "C"

@@ -3,7 +3,6 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <mutex>
 #include <new>
 #include <string>
 
@@ -11,29 +10,13 @@
 #include "f2.hpp"
 #include "pass_desc.h"
 #include "plan.hpp"
+#include "plan_internal.hpp"
 
 namespace bmmc {
 cudaError_t launch_pass(const PassDesc &d, const void *in, void *out, cudaStream_t s);
 }
 
 using namespace bmmc;
-
-struct bmmc_plan_s {
-    int n = 0;
-    int e_log = 0;
-    uint64_t c = 0;
-    f2::Mat a;
-    PlanOptions opt;
-    int npass = 0;
-    f2::Mat t[2];
-    uint64_t tc[2] = {0, 0};
-    PassDesc desc[2];
-    PassInfo info[2];
-    // Workspace owned by the plan for bmmc_execute (two-pass plans only).
-    std::mutex ws_mu;
-    void *ws = nullptr;
-    int ws_device = -1;
-};
 
 namespace {
 

@@ -1,0 +1,170 @@
+// tile_body.cuh -- the per-thread-block body of a tiled pass, shared by the
+// one-array kernel (kernels.cu) and the persistent batch kernel (batch.cu).
+//
+// One call moves thread block `cta` of a pass: 2^it tiles (Sec. 4.1 tiling,
+// Sec. 4.3 several tiles per block).  Every address is an XOR of PassDesc
+// table entries selected by the bits of the block index, the thread index and
+// the loop counter (see plan.cpp for how the tables are derived).
+//
+// Phase 1 (read): each thread copies whole 16-byte chunks of input segments
+//   into shared memory with cp.async (global -> shared, no register staging),
+//   so all of the block's loads are in flight at once.  Lanes of a warp take
+//   consecutive chunks of a segment: every warp load covers whole 128-byte
+//   lines.  The chunk lands at its XOR-swizzled slot.
+// Phase 2 (write): after one barrier, each thread gathers the 16/e elements
+//   of one output chunk from shared memory (conflict-free by the planner's
+//   choice of swizzle and lane assignment, the role of Sec. 4.2's row
+//   rotation) and writes them with one 16-byte store; lanes 0..7 cover one
+//   128-byte output line.
+#pragma once
+#include <stdint.h>
+
+#include "pass_desc.h"
+
+namespace bmmc {
+namespace dev {
+
+__device__ __forceinline__ void cp_async_16(uint32_t smem_addr, const void *gptr)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr),
+                 "l"(gptr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t lds32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint2 lds64(uint32_t addr)
+{
+    uint2 v;
+    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];\n"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void stg128(void *ptr, uint4 v)
+{
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"l"(ptr), "r"(v.x),
+                 "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void swap_if(bool c, T &a, T &b)
+{
+    T ta = c ? b : a;
+    T tb = c ? a : b;
+    a = ta;
+    b = tb;
+}
+
+// One thread block of a tiled pass.  `active` is false for whole warps
+// beyond the pass's 2^thread_bits threads (batch kernel); those warps only
+// take part in the barrier.  sbase: shared-memory byte address of the tile
+// buffer (d.smem_bytes long, 128-byte aligned).
+template <int E_LOG>
+__device__ __forceinline__ void run_tile(const PassDesc &d, uint32_t cta,
+                                         const uint8_t *__restrict__ in,
+                                         uint8_t *__restrict__ out, uint32_t sbase,
+                                         bool active)
+{
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31u;
+    uint32_t t_in = 0, t_dst = 0, t_src = 0, t_out = 0, rot = 0;
+    const uint32_t loop = d.loop;
+    if (active) {
+        // Thread-block part of every address: lane b contributes table entry
+        // b when bit b of the block index is set, and the warp XOR-reduces.
+        const bool bit = (lane < d.n_cta) && ((cta >> lane) & 1u);
+        t_in = __reduce_xor_sync(0xffffffffu, bit ? d.cta_in[lane] : 0u);
+        t_out = __reduce_xor_sync(0xffffffffu, bit ? d.cta_out[lane] : 0u) ^ d.out_const;
+        t_src = __reduce_xor_sync(0xffffffffu, bit ? d.cta_src[lane] : 0u) ^ d.src_const;
+#pragma unroll
+        for (int b = 0; b < kMaxThreadBits; ++b) {
+            if (b < (int)d.thread_bits && ((tid >> b) & 1u)) {
+                t_in ^= d.thr_in[b];
+                t_dst ^= d.thr_dst[b];
+                t_src ^= d.thr_src[b];
+                t_out ^= d.thr_out[b];
+                rot ^= d.thr_rot[b];
+            }
+        }
+        // Phase 1: input segments -> shared memory.
+        for (uint32_t i = 0; i < loop; ++i) {
+            const uint32_t g = t_in ^ d.loop_in[i];
+            const uint32_t s = t_dst ^ d.loop_dst[i];
+            cp_async_16(sbase + (s << E_LOG), in + ((uint64_t)g << E_LOG));
+        }
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    if (!active) return;
+
+    // Phase 2: shared memory -> output chunks.
+    t_src ^= d.elem_src[rot];
+    for (uint32_t i = 0; i < loop; ++i) {
+        const uint32_t s = t_src ^ d.loop_src[i];
+        const uint32_t o = t_out ^ d.loop_out[i];
+        uint4 v;
+        if constexpr (E_LOG == 2) {
+            uint32_t a0 = lds32(sbase + ((s ^ d.elem_src[0]) << 2));
+            uint32_t a1 = lds32(sbase + ((s ^ d.elem_src[1]) << 2));
+            uint32_t a2 = lds32(sbase + ((s ^ d.elem_src[2]) << 2));
+            uint32_t a3 = lds32(sbase + ((s ^ d.elem_src[3]) << 2));
+            // the value loaded by instruction j belongs to element j ^ rot
+            swap_if((rot & 1u) != 0u, a0, a1);
+            swap_if((rot & 1u) != 0u, a2, a3);
+            swap_if((rot & 2u) != 0u, a0, a2);
+            swap_if((rot & 2u) != 0u, a1, a3);
+            v = make_uint4(a0, a1, a2, a3);
+        } else if constexpr (E_LOG == 3) {
+            uint2 a0 = lds64(sbase + ((s ^ d.elem_src[0]) << 3));
+            uint2 a1 = lds64(sbase + ((s ^ d.elem_src[1]) << 3));
+            swap_if((rot & 1u) != 0u, a0, a1);
+            v = make_uint4(a0.x, a0.y, a1.x, a1.y);
+        } else {
+            v = lds128(sbase + ((s ^ d.elem_src[0]) << 4));
+        }
+        stg128(out + ((uint64_t)o << E_LOG), v);
+    }
+}
+
+// Arrays under 1 KiB: thread x < 2^n copies element x to T x + c.
+template <int E_LOG>
+__device__ __forceinline__ void run_naive(const PassDesc &d,
+                                          const uint8_t *__restrict__ in,
+                                          uint8_t *__restrict__ out)
+{
+    const uint32_t x = threadIdx.x;
+    if (x >= (1u << d.n)) return;
+    const uint32_t y = bmmc_map(d.rows, d.n, d.c, x);
+    if constexpr (E_LOG == 2) {
+        reinterpret_cast<uint32_t *>(out)[y] = reinterpret_cast<const uint32_t *>(in)[x];
+    } else if constexpr (E_LOG == 3) {
+        reinterpret_cast<uint2 *>(out)[y] = reinterpret_cast<const uint2 *>(in)[x];
+    } else {
+        reinterpret_cast<uint4 *>(out)[y] = reinterpret_cast<const uint4 *>(in)[x];
+    }
+}
+
+}  // namespace dev
+}  // namespace bmmc

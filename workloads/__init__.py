@@ -30,16 +30,15 @@ def rng(seed):
 
 
 def _rand_bits(g, nbits):
-    """A uniform nbits-bit integer."""
+    """A uniform nbits-bit integer (nbits <= 63)."""
     if nbits == 0:
         return 0
-    v = 0
-    done = 0
-    while done < nbits:
-        take = min(32, nbits - done)
-        v |= int(g.integers(0, 1 << take)) << done
-        done += take
-    return v
+    return int(g.integers(0, 1 << nbits, dtype=np.int64))
+
+
+def _rand_rows(g, n):
+    """n uniform n-bit row masks."""
+    return [int(v) for v in g.integers(0, 1 << n, size=n, dtype=np.int64)]
 
 
 # ---------------------------------------------------------------------------
@@ -85,7 +84,7 @@ def dense_candidates(n, seed):
     """Endless stream of uniform random n x n bit matrices (row masks)."""
     g = rng(seed)
     while True:
-        yield [_rand_bits(g, n) for _ in range(n)]
+        yield _rand_rows(g, n)
 
 
 def first_passing(candidates, accept):
