@@ -532,30 +532,53 @@ def bench_serving(dev, seconds=10.0, rate=2000.0, seed=11, budget=40 * 10**9, st
     pool = torch.randint(-2**31, 2**31 - 1, ((1 << 27) * 8 // 4,), dtype=torch.int32,
                          device=dev, generator=gen)
 
-    def requests():
+    def requests(speedup=1.0, limit_s=None):
         out = []
         for i, (s, (rows, c)) in enumerate(zip(specs, mats)):
+            t = s["arrival"] / speedup
+            if limit_s is not None and t >= limit_s:
+                break
             x = pool[: (1 << s["n"]) * s["e"] // 4]
-            out.append(serving.Request(i, s["arrival"], s["n"], s["e"], rows, c, x))
+            out.append(serving.Request(i, t, s["n"], s["e"], rows, c, x))
         return out
 
-    res = {"requests": len(specs), "rate_per_s": rate, "seconds": seconds,
-           "budget_bytes": budget, "streams": streams}
-    srv = serving.Server(dev, budget_bytes=budget, streams=streams)
-    done, makespan = srv.run(requests())
-    res["server"] = serving.summarize(done, makespan)
-    res["server"]["stats"] = dict(srv.stats)
-    del srv, done
-    torch.cuda.empty_cache()
-    done, makespan = serving.serve_plain(requests(), dev)
-    res["plain"] = serving.summarize(done, makespan)
-    del done, pool
-    torch.cuda.empty_cache()
-    for key in ("server", "plain"):
+    def rounded(d):
         for f in ("throughput_req_s", "effective_gbs", "p50_ms", "p99_ms", "mean_ms",
-                  "makespan_s"):
-            res[key][f] = round(res[key][f], 4)
-    res["p99_ratio_plain_over_server"] = round(res["plain"]["p99_ms"] / res["server"]["p99_ms"], 3)
+                  "makespan_s", "submit_late_p99_ms"):
+            d[f] = round(d[f], 4)
+        return d
+
+    def compare(flags, speedup=1.0, limit_s=None):
+        out = {}
+        for mode, key in (("continuous", "server"), ("plain", "plain")):
+            srv = serving.Server(dev, mode=mode, streams=streams, budget_bytes=budget,
+                                 flags=flags)
+            reqs = serving.drive(srv, requests(speedup, limit_s))
+            out[key] = rounded(serving.summarize(reqs))
+            out[key]["stats"] = srv.stats()
+            srv.close()
+            del srv, reqs
+            torch.cuda.empty_cache()
+        out["p99_ratio_plain_over_server"] = round(out["plain"]["p99_ms"]
+                                                   / out["server"]["p99_ms"], 3)
+        out["throughput_ratio_server_over_plain"] = round(
+            out["server"]["throughput_req_s"] / out["plain"]["throughput_req_s"], 3)
+        return out
+
+    import paper_2306_07795_gb300 as bm
+    res = {"requests": len(specs), "rate_per_s": rate, "seconds": seconds,
+           "budget_bytes": budget, "streams": streams, "strategy": "paper"}
+    res.update(compare(bm.BMMC_PLAN_PAPER))
+    res["single_pass_plans"] = compare(bm.BMMC_PLAN_SINGLE_PASS)
+    # Extra, beyond the configured 2000 requests/s: the same request mix with
+    # arrival times compressed, 2 s per rate.
+    res["extra_rate_sweep"] = []
+    for fast in (4.0, 10.0):
+        row = {"rate_per_s": rate * fast}
+        row.update(compare(bm.BMMC_PLAN_PAPER, speedup=fast, limit_s=2.0))
+        res["extra_rate_sweep"].append(row)
+    del pool
+    torch.cuda.empty_cache()
     return res
 
 

@@ -132,6 +132,22 @@ int bmmc_plan_pass_matrix(bmmc_plan p, int pass, uint64_t *rows_out,
  * Errors: INVALID, OOM. */
 int bmmc_plan_inverse(bmmc_plan p, bmmc_plan *out);
 
+/* The fusion rule of Sec. 3, bmmc(A2, c2) o bmmc(A1, c1) = bmmc(A2 A1,
+ * A2 c1 + c2): create the plan that applies `first` and then `second` as one
+ * permutation.  Both plans must have the same n and element size; the new
+ * plan takes the options of `second`.  Host only.
+ * Errors: INVALID (NULL or mismatched plans), OOM. */
+int bmmc_plan_compose(bmmc_plan second, bmmc_plan first, bmmc_plan *out);
+
+/* The matrix A of the parm combinator (Sec. 6.2), for which
+ *     parm mask f = bmmc(A^{-1}, 0) o parm 2^{n-1} f o bmmc(A, 0):
+ * y_i = x_i for i < lsb(mask), y_i = x_{i+1} for lsb(mask) <= i < n - 1, and
+ * y_{n-1} = x . mask (the F2 dot product).  Moving by (A, 0) puts the
+ * sub-array of the indices with x . mask = 0 in the first half and the other
+ * in the second, each in its original order.  rows_out receives n masks.
+ * Errors: INVALID (n out of 1..32, mask 0 or with bits at positions >= n). */
+int bmmc_parm_matrix(int n, uint64_t mask, uint64_t *rows_out);
+
 /* Device workspace bytes bmmc_execute_ws needs: 2^n * elem_bytes for a
  * two-pass plan, 0 for a one-pass plan.  Returns 0 for a NULL plan. */
 size_t bmmc_plan_workspace_bytes(bmmc_plan p);

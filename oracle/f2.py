@@ -365,6 +365,53 @@ def parm_matrix(n, mask):
     return rows
 
 
+def parm_apply(mask, f, xs):
+    """parm mask f xs by its definition (Sec. 6.1): split xs into the
+    sub-array xs0 of the indices i with i * mask = 0 and xs1 of the others,
+    keeping their order, apply f to each, and put the results back at the
+    positions they came from.  xs is a list of length 2^n."""
+    n = len(xs).bit_length() - 1
+    assert len(xs) == 1 << n and mask and mask < (1 << n)
+    idx = [[], []]
+    for i in range(len(xs)):
+        idx[parm_subarray(i, mask)].append(i)
+    out = [None] * len(xs)
+    for s in (0, 1):
+        ys = f([xs[i] for i in idx[s]])
+        assert len(ys) == len(idx[s])
+        for pos, i in enumerate(idx[s]):
+            out[i] = ys[pos]
+    return out
+
+
+def vcolumn(n, xs):
+    """One V-shaped column of the balanced periodic merger (Sec. 6.1):
+    vcolumn 1 orders a pair; vcolumn n is parm 3 of vcolumn (n - 1)."""
+    if n == 0:
+        return list(xs)
+    if n == 1:
+        a, b = xs
+        return [a, b] if a <= b else [b, a]
+    return parm_apply(3, lambda ys: vcolumn(n - 1, ys), xs)
+
+
+def merge(n, xs):
+    """merge n = parm 2^(n-1) (merge (n - 1)) after vcolumn n (Sec. 6.1)."""
+    if n == 0:
+        return list(xs)
+    ys = vcolumn(n, xs)
+    return parm_apply(1 << (n - 1), lambda zs: merge(n - 1, zs), ys)
+
+
+def sort_network(n, xs):
+    """sort n = merge n after parm 1 (sort (n - 1)) (Sec. 6.1): sort the even
+    and the odd positions, then merge."""
+    if n == 0:
+        return list(xs)
+    ys = parm_apply(1, lambda zs: sort_network(n - 1, zs), xs)
+    return merge(n, ys)
+
+
 # ---------------------------------------------------------------------------
 # Bit partition and stitch functions of a BPC (Sec. 4.1)
 # ---------------------------------------------------------------------------

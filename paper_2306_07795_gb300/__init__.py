@@ -21,5 +21,6 @@ from ._binding import (  # noqa: F401
     bmmc_plan_describe, bmmc_plan_destroy, bmmc_plan_inverse, bmmc_plan_matrix,
     bmmc_plan_num_passes, bmmc_plan_pass_matrix, bmmc_plan_verify,
     bmmc_plan_workspace_bytes, bmmc_strerror, lib, library_path,
+    bmmc_plan_compose, bmmc_parm_matrix,
 )
 from .plan import Plan  # noqa: F401

@@ -33,12 +33,33 @@ EXPORTED = (
     "bmmc_plan_inverse",
     "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws",
     "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
-    "bmmc_strerror",
+    "bmmc_strerror", "bmmc_plan_compose", "bmmc_parm_matrix",
     # include/bmmc_batch.h
     "bmmc_batch_workspace_bytes", "bmmc_batch_table_bytes", "bmmc_batch_create",
     "bmmc_batch_execute",
     "bmmc_batch_num_launches", "bmmc_batch_describe", "bmmc_batch_destroy",
+    # include/bmmc_server.h
+    "bmmc_server_create", "bmmc_server_submit", "bmmc_server_drain",
+    "bmmc_server_results", "bmmc_server_release", "bmmc_server_stats",
+    "bmmc_server_destroy", "bmmc_server_hold", "bmmc_server_now_ms",
 )
+
+BMMC_SERVER_CONTINUOUS = 0
+BMMC_SERVER_PLAIN = 1
+
+
+class bmmc_server_config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("streams", ctypes.c_int),
+                ("budget_bytes", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
+                ("plan_flags", ctypes.c_uint32), ("group_max_bytes", ctypes.c_uint64),
+                ("group_min", ctypes.c_int), ("keep_outputs", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class bmmc_server_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("submit_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("out", ctypes.c_void_p)]
 
 
 class BmmcError(RuntimeError):
@@ -91,6 +112,8 @@ def lib():
         "bmmc_plan_verify": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "bmmc_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "bmmc_plan_compose": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
+        "bmmc_parm_matrix": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, u64p]),
         "bmmc_batch_workspace_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_table_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), vpp, ctypes.c_int,
@@ -99,6 +122,18 @@ def lib():
         "bmmc_batch_num_launches": (ctypes.c_int, [vp]),
         "bmmc_batch_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_batch_destroy": (None, [vp]),
+        "bmmc_server_create": (ctypes.c_int, [ctypes.POINTER(vp),
+                                              ctypes.POINTER(bmmc_server_config)]),
+        "bmmc_server_submit": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int, u64p,
+                                              ctypes.c_uint64, ctypes.c_size_t, vp]),
+        "bmmc_server_drain": (ctypes.c_int, [vp]),
+        "bmmc_server_results": (ctypes.c_int, [vp, ctypes.POINTER(bmmc_server_result),
+                                               ctypes.c_int]),
+        "bmmc_server_release": (ctypes.c_int, [vp, vp]),
+        "bmmc_server_stats": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "bmmc_server_destroy": (None, [vp]),
+        "bmmc_server_hold": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bmmc_server_now_ms": (ctypes.c_double, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -200,6 +235,18 @@ def bmmc_strerror(code):
     return lib().bmmc_strerror(code).decode()
 
 
+def bmmc_plan_compose(second, first):
+    out = ctypes.c_void_p()
+    _check(lib().bmmc_plan_compose(second, first, ctypes.byref(out)), "bmmc_plan_compose")
+    return out
+
+
+def bmmc_parm_matrix(n, mask):
+    rows = (ctypes.c_uint64 * n)()
+    _check(lib().bmmc_parm_matrix(n, mask, rows), "bmmc_parm_matrix")
+    return [int(r) for r in rows]
+
+
 # ---------------------------------------------------------------------------
 # include/bmmc_batch.h
 # ---------------------------------------------------------------------------
@@ -247,3 +294,58 @@ def bmmc_batch_describe(h):
 
 def bmmc_batch_destroy(h):
     lib().bmmc_batch_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# include/bmmc_server.h
+# ---------------------------------------------------------------------------
+
+def bmmc_server_create(cfg):
+    h = ctypes.c_void_p()
+    _check(lib().bmmc_server_create(ctypes.byref(h), ctypes.byref(cfg)),
+           "bmmc_server_create")
+    return h
+
+
+def bmmc_server_submit(h, rid, n, rows, c, elem_bytes, in_ptr):
+    """Returns the status code (a request rejected at submission is not queued)."""
+    return lib().bmmc_server_submit(h, rid, n, _rows(rows), c, elem_bytes, in_ptr)
+
+
+def bmmc_server_drain(h):
+    _check(lib().bmmc_server_drain(h), "bmmc_server_drain")
+
+
+def bmmc_server_results(h, max_results=4096):
+    buf = (bmmc_server_result * max_results)()
+    out = []
+    while True:
+        k = lib().bmmc_server_results(h, buf, max_results)
+        if k < 0:
+            _check(k, "bmmc_server_results")
+        out.extend((r.id, r.status, r.submit_ms, r.done_ms, r.out) for r in buf[:k])
+        if k < max_results:
+            return out
+
+
+def bmmc_server_release(h, ptr):
+    _check(lib().bmmc_server_release(h, ptr), "bmmc_server_release")
+
+
+def bmmc_server_stats(h):
+    need = lib().bmmc_server_stats(h, None, 0)
+    buf = ctypes.create_string_buffer(need + 1)
+    lib().bmmc_server_stats(h, buf, need + 1)
+    return json.loads(buf.value.decode())
+
+
+def bmmc_server_destroy(h):
+    lib().bmmc_server_destroy(h)
+
+
+def bmmc_server_hold(h, hold):
+    _check(lib().bmmc_server_hold(h, 1 if hold else 0), "bmmc_server_hold")
+
+
+def bmmc_server_now_ms(h):
+    return float(lib().bmmc_server_now_ms(h))

@@ -190,6 +190,37 @@ int bmmc_plan_inverse(bmmc_plan p, bmmc_plan *out)
     return create_impl(out, p->n, inv.r, inv.apply(p->c), (size_t)1 << p->e_log, &o);
 }
 
+int bmmc_plan_compose(bmmc_plan second, bmmc_plan first, bmmc_plan *out)
+{
+    if (!out) return BMMC_ERR_INVALID;
+    *out = nullptr;
+    if (!second || !first || second->n != first->n || second->e_log != first->e_log)
+        return BMMC_ERR_INVALID;
+    // (A2, c2) o (A1, c1) = (A2 A1, A2 c1 + c2)
+    f2::Mat a = f2::mul(second->a, first->a);
+    const uint64_t c = second->a.apply(first->c) ^ second->c;
+    bmmc_plan_options o;
+    memset(&o, 0, sizeof(o));
+    o.flags = second->opt.flags;
+    o.seg_bits = second->opt.seg_bits;
+    o.cta_tile_log2 = second->opt.cta_tile_log2;
+    return create_impl(out, second->n, a.r, c, (size_t)1 << second->e_log, &o);
+}
+
+int bmmc_parm_matrix(int n, uint64_t mask, uint64_t *rows_out)
+{
+    if (n < 1 || n > kMaxN || !rows_out) return BMMC_ERR_INVALID;
+    const uint64_t nmask = (1ull << n) - 1;
+    if (mask == 0 || (mask & ~nmask)) return BMMC_ERR_INVALID;
+    const int low = __builtin_ctzll(mask);
+    for (int i = 0; i < n; ++i) {
+        if (i == n - 1) rows_out[i] = mask;                // y_{n-1} = x . mask
+        else if (i < low) rows_out[i] = 1ull << i;         // y_i = x_i
+        else rows_out[i] = 1ull << (i + 1);                // y_i = x_{i+1}
+    }
+    return BMMC_OK;
+}
+
 size_t bmmc_plan_workspace_bytes(bmmc_plan p)
 {
     if (!p || p->npass < 2) return 0;

@@ -1,0 +1,622 @@
+// server.cpp -- native request server (include/bmmc_server.h).
+//
+// Submission plans the request in the caller's thread (bmmc_plan_create_ex),
+// so planning cost scales with the number of submitting threads.  In
+// CONTINUOUS mode a scheduler thread then admits requests in submission order
+// while their input + output + workspace bytes fit the budget and their output
+// and workspace fit the arena, launches each on the least-loaded stream (small
+// ones admitted together share one batch launch), and retires launches as
+// their events complete.  PLAIN mode does planning, allocation and launch in
+// the submitting thread on one stream.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bmmc.h"
+#include "bmmc_batch.h"
+#include "bmmc_server.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxStreams = 32;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit allocator over one device block; free ranges kept coalesced.
+class Arena {
+public:
+    void init(uint8_t *base, size_t size)
+    {
+        base_ = base;
+        size_ = size;
+        free_.clear();
+        free_[0] = size;
+    }
+    void *alloc(size_t bytes)
+    {
+        bytes = align_up(bytes ? bytes : 1);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > bytes) free_[off + bytes] = len - bytes;
+                used_ += bytes;
+                return base_ + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void *p, size_t bytes)
+    {
+        if (!p) return;
+        bytes = align_up(bytes ? bytes : 1);
+        size_t off = (uint8_t *)p - base_;
+        used_ -= bytes;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + bytes == next->first) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+    size_t size() const { return size_; }
+    size_t used() const { return used_; }
+
+private:
+    uint8_t *base_ = nullptr;
+    size_t size_ = 0;
+    size_t used_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Req {
+    uint64_t id = 0;
+    const void *in = nullptr;
+    bmmc_plan plan = nullptr;
+    size_t array_bytes = 0;  // 2^n * e
+    size_t ws_bytes = 0;
+    uint64_t bytes = 0;      // in + out + ws, for the budget
+    void *out = nullptr;
+    void *ws = nullptr;
+    double submit_ms = 0;
+    int status = BMMC_OK;
+};
+
+struct Launch {
+    std::vector<Req *> reqs;
+    cudaEvent_t ev = nullptr;
+    bmmc_batch batch = nullptr;
+    void *table = nullptr;
+    size_t table_bytes = 0;
+    void *group_ws = nullptr;
+    size_t group_ws_bytes = 0;
+};
+
+}  // namespace
+
+struct bmmc_server_s {
+    bmmc_server_config cfg;
+    int device = -1;
+    int nstreams = 1;
+    cudaStream_t streams[kMaxStreams] = {};
+    cudaEvent_t start = nullptr;
+    std::chrono::steady_clock::time_point t0;
+    uint8_t *arena_mem = nullptr;
+    Arena arena;           // guarded by sched_mu
+    std::vector<cudaEvent_t> events;  // free events, guarded by sched_mu
+
+    // submission side
+    std::mutex mu;
+    std::condition_variable cv;       // new submissions / stop
+    std::condition_variable drained;  // outstanding reached 0
+    std::deque<Req *> submitted;
+    std::vector<bmmc_server_result> results;
+    uint64_t outstanding = 0;
+    bool stop = false;
+    bool hold = false;
+    std::thread worker;
+
+    // scheduler side (worker thread in CONTINUOUS; callers under sched_mu in PLAIN)
+    std::mutex sched_mu;
+    std::deque<Req *> waiting;
+    std::deque<Launch> inflight[kMaxStreams];
+    std::map<void *, size_t> kept;  // kept outputs and their sizes
+    uint64_t used = 0;
+
+    // counters
+    uint64_t n_submitted = 0, n_completed = 0, n_single = 0, n_groups = 0,
+             n_grouped = 0, peak_bytes = 0, peak_inflight = 0, n_inflight = 0;
+
+    double now_ms() const
+    {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+            .count();
+    }
+};
+
+namespace {
+
+cudaEvent_t take_event(bmmc_server_s *s)
+{
+    if (s->events.empty()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    cudaEvent_t e = s->events.back();
+    s->events.pop_back();
+    return e;
+}
+
+// Completion of one launch (sched_mu held).  Records results, frees bytes.
+void finish(bmmc_server_s *s, Launch &L)
+{
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->start, L.ev);
+    std::vector<bmmc_server_result> done;
+    done.reserve(L.reqs.size());
+    for (Req *r : L.reqs) {
+        s->used -= r->bytes;
+        if (r->ws) s->arena.release(r->ws, r->ws_bytes);
+        bmmc_server_result res;
+        res.id = r->id;
+        res.status = r->status;
+        res.submit_ms = r->submit_ms;
+        res.done_ms = ms;
+        res.out = r->out;
+        if (!s->cfg.keep_outputs) {
+            s->arena.release(r->out, r->array_bytes);
+            res.out = nullptr;
+        } else {
+            s->kept[r->out] = r->array_bytes;
+        }
+        done.push_back(res);
+        bmmc_plan_destroy(r->plan);
+        delete r;
+    }
+    if (L.batch) bmmc_batch_destroy(L.batch);
+    if (L.table) s->arena.release(L.table, L.table_bytes);
+    if (L.group_ws) s->arena.release(L.group_ws, L.group_ws_bytes);
+    s->events.push_back(L.ev);
+    s->n_inflight -= L.reqs.size();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->results.insert(s->results.end(), done.begin(), done.end());
+        s->n_completed += done.size();
+        s->outstanding -= done.size();
+        if (s->outstanding == 0) s->drained.notify_all();
+    }
+}
+
+// Retire completed launches at the heads of the stream queues.
+bool retire(bmmc_server_s *s)
+{
+    bool any = false;
+    for (int i = 0; i < s->nstreams; ++i) {
+        auto &q = s->inflight[i];
+        while (!q.empty() && cudaEventQuery(q.front().ev) == cudaSuccess) {
+            finish(s, q.front());
+            q.pop_front();
+            any = true;
+        }
+    }
+    cudaGetLastError();  // clear cudaErrorNotReady
+    return any;
+}
+
+int least_loaded(bmmc_server_s *s)
+{
+    int best = 0;
+    for (int i = 1; i < s->nstreams; ++i)
+        if (s->inflight[i].size() < s->inflight[best].size()) best = i;
+    return best;
+}
+
+void note_peaks(bmmc_server_s *s)
+{
+    s->peak_bytes = std::max<uint64_t>(s->peak_bytes, s->used);
+    s->peak_inflight = std::max<uint64_t>(s->peak_inflight, s->n_inflight);
+}
+
+// Launch one request on stream si (sched_mu held, buffers allocated).  A
+// request that fails to launch still completes, with its error status, once
+// the stream reaches its event.
+void launch_single(bmmc_server_s *s, Req *r, int si)
+{
+    Launch L;
+    L.ev = take_event(s);
+    int rc = bmmc_execute_ws(r->plan, r->in, r->out, r->ws, (bmmc_stream_t)s->streams[si]);
+    if (rc != BMMC_OK) r->status = rc;
+    if (!L.ev || cudaEventRecord(L.ev, s->streams[si]) != cudaSuccess) {
+        // no event: wait here so that completion is known
+        cudaStreamSynchronize(s->streams[si]);
+        if (!L.ev) cudaEventCreate(&L.ev);
+        cudaEventRecord(L.ev, s->streams[si]);
+        if (r->status == BMMC_OK) r->status = BMMC_ERR_CUDA;
+    }
+    L.reqs.push_back(r);
+    s->inflight[si].push_back(L);
+    s->n_single += 1;
+    s->n_inflight += 1;
+}
+
+// Try to launch several admitted small requests as one batch.  On failure
+// (no arena room for its tables) returns false and launches nothing.
+bool launch_group(bmmc_server_s *s, std::vector<Req *> &g, int si)
+{
+    std::vector<bmmc_plan> plans;
+    std::vector<const void *> ins;
+    std::vector<void *> outs;
+    for (Req *r : g) {
+        plans.push_back(r->plan);
+        ins.push_back(r->in);
+        outs.push_back(r->out);
+    }
+    Launch L;
+    L.table_bytes = bmmc_batch_table_bytes(plans.data(), (int)g.size());
+    L.group_ws_bytes = bmmc_batch_workspace_bytes(plans.data(), (int)g.size());
+    L.table = s->arena.alloc(L.table_bytes);
+    if (!L.table) return false;
+    if (L.group_ws_bytes) {
+        L.group_ws = s->arena.alloc(L.group_ws_bytes);
+        if (!L.group_ws) {
+            s->arena.release(L.table, L.table_bytes);
+            return false;
+        }
+    }
+    int rc = bmmc_batch_create(&L.batch, plans.data(), (int)g.size(), ins.data(), outs.data(),
+                               L.group_ws, L.table, (bmmc_stream_t)s->streams[si]);
+    if (rc != BMMC_OK) {
+        s->arena.release(L.table, L.table_bytes);
+        if (L.group_ws) s->arena.release(L.group_ws, L.group_ws_bytes);
+        return false;
+    }
+    L.ev = take_event(s);
+    if (!L.ev) {
+        bmmc_batch_destroy(L.batch);
+        s->arena.release(L.table, L.table_bytes);
+        if (L.group_ws) s->arena.release(L.group_ws, L.group_ws_bytes);
+        return false;
+    }
+    const int rc_exec = bmmc_batch_execute(L.batch, (bmmc_stream_t)s->streams[si]);
+    cudaEventRecord(L.ev, s->streams[si]);
+    if (rc_exec != BMMC_OK)
+        for (Req *r : g) r->status = rc_exec;
+    // grouped requests use the group workspace, not their own
+    for (Req *r : g) {
+        if (r->ws) s->arena.release(r->ws, r->ws_bytes);
+        r->ws = nullptr;
+    }
+    L.reqs = g;
+    s->inflight[si].push_back(L);
+    s->n_groups += 1;
+    s->n_grouped += g.size();
+    s->n_inflight += g.size();
+    return true;
+}
+
+// Allocate a request's output (and workspace); false if the arena is full.
+bool allocate(bmmc_server_s *s, Req *r)
+{
+    r->out = s->arena.alloc(r->array_bytes);
+    if (!r->out) return false;
+    if (r->ws_bytes) {
+        r->ws = s->arena.alloc(r->ws_bytes);
+        if (!r->ws) {
+            s->arena.release(r->out, r->array_bytes);
+            r->out = nullptr;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Admit waiting requests in order while they fit; launch them.  Returns true
+// if anything was launched.
+bool admit(bmmc_server_s *s)
+{
+    std::vector<Req *> admitted;
+    while (!s->waiting.empty()) {
+        Req *r = s->waiting.front();
+        const bool idle = (s->used == 0 && admitted.empty());
+        if (!idle && s->used + r->bytes > s->cfg.budget_bytes) break;
+        if (!allocate(s, r)) break;
+        s->waiting.pop_front();
+        s->used += r->bytes;
+        admitted.push_back(r);
+    }
+    if (admitted.empty()) return false;
+    std::vector<Req *> small;
+    for (Req *r : admitted) {
+        if (s->cfg.group_max_bytes && r->array_bytes <= s->cfg.group_max_bytes)
+            small.push_back(r);
+    }
+    const bool group = s->cfg.group_min > 0 && (int)small.size() >= s->cfg.group_min;
+    if (group && launch_group(s, small, least_loaded(s))) {
+        for (Req *r : admitted)
+            if (r->array_bytes > s->cfg.group_max_bytes) launch_single(s, r, least_loaded(s));
+    } else {
+        for (Req *r : admitted) launch_single(s, r, least_loaded(s));
+    }
+    note_peaks(s);
+    return true;
+}
+
+void worker_main(bmmc_server_s *s)
+{
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::deque<Req *> fresh;
+        bool busy;
+        {
+            std::lock_guard<std::mutex> lk2(s->sched_mu);
+            busy = !s->waiting.empty() || s->n_inflight != 0;
+        }
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if ((!busy && s->submitted.empty()) || (s->hold && !s->stop)) {
+                if (s->stop && s->submitted.empty() && !busy) return;
+                s->cv.wait_for(lk, std::chrono::milliseconds(1));
+                if (s->hold && !s->stop) {
+                    lk.unlock();
+                    std::lock_guard<std::mutex> lk2(s->sched_mu);
+                    retire(s);  // keep retiring while admission is held
+                    continue;
+                }
+            }
+            fresh.swap(s->submitted);
+        }
+        std::lock_guard<std::mutex> lk2(s->sched_mu);
+        for (Req *r : fresh) s->waiting.push_back(r);
+        bool progress = retire(s);
+        progress |= admit(s);
+        if (!progress && s->n_inflight) std::this_thread::yield();
+    }
+}
+
+// Plan a request (caller's thread).
+int prepare(bmmc_server_s *s, Req *r, int n, const uint64_t *rows, uint64_t c, size_t e)
+{
+    bmmc_plan_options o;
+    memset(&o, 0, sizeof(o));
+    o.flags = s->cfg.plan_flags;
+    int rc = bmmc_plan_create_ex(&r->plan, n, rows, c, e, &o);
+    if (rc != BMMC_OK) return rc;
+    r->array_bytes = ((size_t)1 << n) * e;
+    r->ws_bytes = bmmc_plan_workspace_bytes(r->plan);
+    r->bytes = 2 * (uint64_t)r->array_bytes + r->ws_bytes;
+    if (align_up(r->array_bytes) + align_up(r->ws_bytes) > s->arena.size()) {
+        bmmc_plan_destroy(r->plan);
+        r->plan = nullptr;
+        return BMMC_ERR_TOO_LARGE;
+    }
+    return BMMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bmmc_server_create(bmmc_server *out, const bmmc_server_config *cfg)
+{
+    if (!out || !cfg) return BMMC_ERR_INVALID;
+    *out = nullptr;
+    for (int r : cfg->reserved)
+        if (r) return BMMC_ERR_UNSUPPORTED;
+    if (cfg->mode != BMMC_SERVER_CONTINUOUS && cfg->mode != BMMC_SERVER_PLAIN)
+        return BMMC_ERR_UNSUPPORTED;
+    if (cfg->streams < 1 || cfg->streams > kMaxStreams) return BMMC_ERR_UNSUPPORTED;
+    if (cfg->arena_bytes < kAlign || cfg->budget_bytes == 0) return BMMC_ERR_UNSUPPORTED;
+    if (cfg->plan_flags > BMMC_PLAN_SINGLE_PASS) return BMMC_ERR_UNSUPPORTED;
+    bmmc_server_s *s = new (std::nothrow) bmmc_server_s();
+    if (!s) return BMMC_ERR_OOM;
+    s->cfg = *cfg;
+    s->nstreams = cfg->mode == BMMC_SERVER_PLAIN ? 1 : cfg->streams;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return BMMC_ERR_CUDA;
+    }
+    if (cudaMalloc((void **)&s->arena_mem, cfg->arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return BMMC_ERR_OOM;
+    }
+    s->arena.init(s->arena_mem, cfg->arena_bytes);
+    for (int i = 0; i < s->nstreams; ++i)
+        cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) == cudaSuccess) s->events.push_back(e);
+    }
+    cudaEventCreate(&s->start);
+    cudaDeviceSynchronize();
+    cudaEventRecord(s->start, s->streams[0]);
+    cudaEventSynchronize(s->start);
+    s->t0 = std::chrono::steady_clock::now();
+    if (cudaGetLastError() != cudaSuccess) {
+        bmmc_server_destroy(s);
+        return BMMC_ERR_CUDA;
+    }
+    if (cfg->mode == BMMC_SERVER_CONTINUOUS) s->worker = std::thread(worker_main, s);
+    *out = s;
+    return BMMC_OK;
+}
+
+int bmmc_server_submit(bmmc_server s, uint64_t id, int n, const uint64_t *A_rows, uint64_t c,
+                       size_t elem_bytes, const void *in)
+{
+    if (!s || !in) return BMMC_ERR_INVALID;
+    if ((uintptr_t)in & 15u) return BMMC_ERR_ALIGN;
+    Req *r = new (std::nothrow) Req();
+    if (!r) return BMMC_ERR_OOM;
+    r->id = id;
+    r->in = in;
+    r->submit_ms = s->now_ms();
+    int rc = prepare(s, r, n, A_rows, c, elem_bytes);
+    if (rc != BMMC_OK) {
+        delete r;
+        return rc;
+    }
+    if (s->cfg.mode == BMMC_SERVER_CONTINUOUS) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->submitted.push_back(r);
+        s->outstanding += 1;
+        s->n_submitted += 1;
+        s->cv.notify_one();
+        return BMMC_OK;
+    }
+    // PLAIN: allocate (waiting for completions if the arena is full), launch.
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->outstanding += 1;
+        s->n_submitted += 1;
+    }
+    std::lock_guard<std::mutex> lk(s->sched_mu);
+    retire(s);
+    while (!allocate(s, r)) {
+        if (s->inflight[0].empty()) {  // cannot happen: prepare checked the size
+            bmmc_plan_destroy(r->plan);
+            delete r;
+            return BMMC_ERR_OOM;
+        }
+        cudaEventSynchronize(s->inflight[0].front().ev);
+        retire(s);
+    }
+    s->used += r->bytes;
+    launch_single(s, r, 0);
+    note_peaks(s);
+    return BMMC_OK;
+}
+
+int bmmc_server_drain(bmmc_server s)
+{
+    if (!s) return BMMC_ERR_INVALID;
+    if (s->cfg.mode == BMMC_SERVER_CONTINUOUS) {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->drained.wait(lk, [s] { return s->outstanding == 0; });
+        return BMMC_OK;
+    }
+    std::lock_guard<std::mutex> lk(s->sched_mu);
+    while (!s->inflight[0].empty()) {
+        cudaEventSynchronize(s->inflight[0].front().ev);
+        retire(s);
+    }
+    return BMMC_OK;
+}
+
+int bmmc_server_hold(bmmc_server s, int hold)
+{
+    if (!s) return BMMC_ERR_INVALID;
+    if (s->cfg.mode != BMMC_SERVER_CONTINUOUS) return BMMC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->hold = hold != 0;
+    s->cv.notify_all();
+    return BMMC_OK;
+}
+
+double bmmc_server_now_ms(bmmc_server s) { return s ? s->now_ms() : -1.0; }
+
+int bmmc_server_results(bmmc_server s, bmmc_server_result *res, int max)
+{
+    if (!s || (!res && max > 0) || max < 0) return BMMC_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    int k = (int)std::min<size_t>((size_t)max, s->results.size());
+    for (int i = 0; i < k; ++i) res[i] = s->results[i];
+    s->results.erase(s->results.begin(), s->results.begin() + k);
+    return k;
+}
+
+int bmmc_server_release(bmmc_server s, void *out)
+{
+    if (!s || !out) return BMMC_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->sched_mu);
+    auto it = s->kept.find(out);
+    if (it == s->kept.end()) return BMMC_ERR_INVALID;
+    s->arena.release(it->first, it->second);
+    s->kept.erase(it);
+    return BMMC_OK;
+}
+
+int bmmc_server_stats(bmmc_server s, char *buf, size_t len)
+{
+    if (!s) return BMMC_ERR_INVALID;
+    char tmp[512];
+    uint64_t single, groups, grouped, peak_b, peak_i, sub, comp;
+    {
+        std::lock_guard<std::mutex> lk(s->sched_mu);
+        single = s->n_single;
+        groups = s->n_groups;
+        grouped = s->n_grouped;
+        peak_b = s->peak_bytes;
+        peak_i = s->peak_inflight;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        sub = s->n_submitted;
+        comp = s->n_completed;
+    }
+    int k = snprintf(tmp, sizeof(tmp),
+                     "{\"mode\": \"%s\", \"streams\": %d, \"submitted\": %llu, "
+                     "\"completed\": %llu, \"single_launches\": %llu, "
+                     "\"group_launches\": %llu, \"grouped_requests\": %llu, "
+                     "\"peak_bytes_in_flight\": %llu, \"peak_requests_in_flight\": %llu}",
+                     s->cfg.mode == BMMC_SERVER_PLAIN ? "plain" : "continuous", s->nstreams,
+                     (unsigned long long)sub, (unsigned long long)comp,
+                     (unsigned long long)single, (unsigned long long)groups,
+                     (unsigned long long)grouped, (unsigned long long)peak_b,
+                     (unsigned long long)peak_i);
+    if (buf && len) {
+        size_t cpy = (size_t)k < len - 1 ? (size_t)k : len - 1;
+        memcpy(buf, tmp, cpy);
+        buf[cpy] = 0;
+    }
+    return k;
+}
+
+void bmmc_server_destroy(bmmc_server s)
+{
+    if (!s) return;
+    if (s->worker.joinable()) {
+        bmmc_server_hold(s, 0);
+        bmmc_server_drain(s);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+            s->cv.notify_all();
+        }
+        s->worker.join();
+    } else if (s->cfg.mode == BMMC_SERVER_PLAIN) {
+        bmmc_server_drain(s);
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (s->device >= 0) cudaSetDevice(s->device);
+    for (int i = 0; i < s->nstreams; ++i)
+        if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
+    for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+    if (s->start) cudaEventDestroy(s->start);
+    if (s->arena_mem) cudaFree(s->arena_mem);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete s;
+}
+
+}  // extern "C"

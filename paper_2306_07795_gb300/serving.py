@@ -1,79 +1,27 @@
-"""Request serving: continuous admission of BMMC permutation requests.
+"""Request serving over the native server of include/bmmc_server.h.
 
-Requests arrive over time (each: n, element size, matrix A, complement c,
-input array already on the device).  The server
+Server(mode="continuous") admits requests as they arrive under an HBM budget
+onto S streams (small ones grouped into batch launches); Server(mode="plain")
+is the one-launch-per-request baseline.  Both plan in the submitting thread,
+inside the library, and time completions with CUDA events; see the header for
+the scheduling rules.
 
-* admits a request as soon as it has arrived, a stream slot is free and its
-  device bytes (input + output + workspace) fit in the HBM budget;
-* keeps plans in a cache keyed by (n, e, A, c) and output/workspace buffers
-  in a pool keyed by size, so steady-state admission allocates nothing new;
-* runs admitted requests on S streams, so requests that arrive while others
-  are on the GPU start at once and overlap with them on the device; small
-  requests admitted in the same scheduling round share one persistent batch
-  launch when there are several;
-* retires requests as their completion events fire, returning bytes and
-  slots, and records each completion time on the GPU clock.
-
-Latency of a request = completion (CUDA event, relative to a start event
-recorded when the run begins) - arrival (host clock, relative to the same
-instant).  The plain baseline, ``serve_plain``, launches one request at a
-time in arrival order on one stream.
+drive(server, requests) submits each request at its arrival time (seconds
+from the start of the run) and returns per-request latencies.
 """
 
-import collections
 import time
 
 from . import _binding as B
-from .plan import Plan
-
-
-class PlanCache:
-    """LRU cache of plans keyed by (n, e, rows, c, flags)."""
-
-    def __init__(self, capacity=4096):
-        self.capacity = capacity
-        self._d = collections.OrderedDict()
-        self.hits = 0
-        self.misses = 0
-
-    def get(self, n, rows, c, e, flags):
-        key = (n, e, tuple(rows), c, flags)
-        p = self._d.get(key)
-        if p is not None:
-            self._d.move_to_end(key)
-            self.hits += 1
-            return p
-        self.misses += 1
-        p = Plan(n, rows, c, e, flags=flags)
-        self._d[key] = p
-        if len(self._d) > self.capacity:
-            self._d.popitem(last=False)
-        return p
-
-
-class BufferPool:
-    """Device byte buffers reused by exact size."""
-
-    def __init__(self, device):
-        self.device = device
-        self._free = collections.defaultdict(list)
-        self.allocated_bytes = 0
-
-    def take(self, nbytes):
-        import torch
-        lst = self._free.get(nbytes)
-        if lst:
-            return lst.pop()
-        self.allocated_bytes += nbytes
-        return torch.empty(nbytes, dtype=torch.uint8, device=self.device)
-
-    def give(self, buf):
-        self._free[buf.numel()].append(buf)
 
 
 class Request:
-    __slots__ = ("rid", "arrival", "n", "e", "rows", "c", "x", "out", "ws",
-                 "plan", "done_event", "slot", "bytes", "completion")
+    """One permutation request: an array of 2^n elements of e bytes already
+    on the device (x), a matrix (rows) and complement c, arriving at
+    `arrival` seconds."""
+
+    __slots__ = ("rid", "arrival", "n", "e", "rows", "c", "x", "status",
+                 "submit_ms", "done_ms", "out_ptr", "late_ms", "arrival_ms")
 
     def __init__(self, rid, arrival, n, e, rows, c, x):
         self.rid = rid
@@ -83,13 +31,104 @@ class Request:
         self.rows = rows
         self.c = c
         self.x = x
-        self.out = None
-        self.ws = None
-        self.plan = None
-        self.done_event = None
-        self.slot = None
-        self.bytes = 0
-        self.completion = None
+        self.status = None
+        self.submit_ms = None
+        self.done_ms = None
+        self.out_ptr = None
+        self.late_ms = None
+        self.arrival_ms = None
+
+    @property
+    def latency_ms(self):
+        """Completion minus scheduled arrival (server clock), so a submitter
+        that falls behind does not hide queueing."""
+        return self.done_ms - self.arrival_ms
+
+
+class Server:
+    def __init__(self, device, mode="continuous", streams=4, budget_bytes=40 * 10**9,
+                 arena_bytes=None, flags=B.BMMC_PLAN_PAPER, group_max_bytes=1 << 22,
+                 group_min=4, keep_outputs=False):
+        import torch
+        self.device = torch.device(device)
+        cfg = B.bmmc_server_config()
+        cfg.mode = B.BMMC_SERVER_PLAIN if mode == "plain" else B.BMMC_SERVER_CONTINUOUS
+        cfg.streams = streams
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.arena_bytes = int(arena_bytes if arena_bytes is not None else budget_bytes)
+        cfg.plan_flags = flags
+        cfg.group_max_bytes = int(group_max_bytes)
+        cfg.group_min = group_min
+        cfg.keep_outputs = 1 if keep_outputs else 0
+        self.mode = mode
+        with torch.cuda.device(self.device):
+            self._h = B.bmmc_server_create(cfg)
+
+    def submit(self, rid, n, rows, c, elem_bytes, x):
+        """Queue one request (x: contiguous CUDA tensor of 2^n * elem_bytes
+        bytes).  Returns the library status code."""
+        return B.bmmc_server_submit(self._h, rid, n, rows, c, elem_bytes, x.data_ptr())
+
+    def drain(self):
+        B.bmmc_server_drain(self._h)
+
+    def hold(self, on=True):
+        """Stop (on) or resume admission; queued requests are admitted together
+        on resume."""
+        B.bmmc_server_hold(self._h, on)
+
+    def now_ms(self):
+        return B.bmmc_server_now_ms(self._h)
+
+    def results(self):
+        return B.bmmc_server_results(self._h)
+
+    def release(self, ptr):
+        B.bmmc_server_release(self._h, ptr)
+
+    def stats(self):
+        return B.bmmc_server_stats(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            B.bmmc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def drive(server, requests, spin_s=200e-6):
+    """Submit `requests` (sorted by arrival) at their arrival times, wait for
+    all of them, and fill in status, submit/done times and outputs.  Returns
+    the requests."""
+    import torch
+    with torch.cuda.device(server.device):
+        origin_ms = server.now_ms()  # driver time 0 on the server's clock
+        t_start = time.perf_counter()
+        by_id = {}
+        for r in requests:
+            while True:
+                wait = r.arrival - (time.perf_counter() - t_start)
+                if wait <= 0:
+                    break
+                if wait > spin_s:
+                    time.sleep(wait - spin_s)
+            r.late_ms = ((time.perf_counter() - t_start) - r.arrival) * 1e3
+            r.arrival_ms = origin_ms + r.arrival * 1e3
+            r.status = server.submit(r.rid, r.n, r.rows, r.c, r.e, r.x)
+            by_id[r.rid] = r
+        server.drain()
+        for rid, status, sub, done, out in server.results():
+            r = by_id[rid]
+            r.status = status
+            r.submit_ms = sub
+            r.done_ms = done
+            r.out_ptr = out
+    return requests
 
 
 def _percentile(values, q):
@@ -102,193 +141,16 @@ def _percentile(values, q):
     return v[lo] + (v[hi] - v[lo]) * (k - lo)
 
 
-def summarize(requests, makespan_s):
-    lat = [(r.completion - r.arrival) * 1e3 for r in requests]
-    moved = sum(2 * (1 << r.n) * r.e for r in requests)
-    return {"requests": len(requests),
-            "throughput_req_s": len(requests) / makespan_s,
-            "effective_gbs": moved / makespan_s / 1e9,
+def summarize(requests):
+    ok = [r for r in requests if r.status == B.BMMC_OK and r.done_ms is not None]
+    lat = [r.latency_ms for r in ok]
+    first = min(r.arrival_ms for r in ok)
+    last = max(r.done_ms for r in ok)
+    span_s = (last - first) / 1e3
+    moved = sum(2 * (1 << r.n) * r.e for r in ok)
+    late = [r.late_ms for r in requests if r.late_ms is not None]
+    return {"requests": len(requests), "completed": len(ok),
+            "throughput_req_s": len(ok) / span_s, "effective_gbs": moved / span_s / 1e9,
             "p50_ms": _percentile(lat, 0.50), "p99_ms": _percentile(lat, 0.99),
-            "mean_ms": sum(lat) / len(lat) if lat else None,
-            "makespan_s": makespan_s}
-
-
-class Server:
-    def __init__(self, device, budget_bytes=40 * 10**9, streams=4,
-                 flags=B.BMMC_PLAN_PAPER, batch_threshold_bytes=1 << 22,
-                 plan_cache=None):
-        import torch
-        self.device = device
-        self.budget = budget_bytes
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
-        self.flags = flags
-        self.batch_threshold = batch_threshold_bytes
-        self.plans = plan_cache or PlanCache()
-        self.pool = BufferPool(device)
-        self.stats = {"admitted_rounds": 0, "batched_launches": 0, "single_launches": 0,
-                      "max_in_flight_bytes": 0, "max_in_flight": 0}
-
-    def _plan(self, r):
-        r.plan = self.plans.get(r.n, r.rows, r.c, r.e, self.flags)
-        r.bytes = 2 * (1 << r.n) * r.e + r.plan.workspace_bytes  # in + out + ws
-
-    def _buffers(self, r):
-        r.out = self.pool.take((1 << r.n) * r.e)
-        wsb = r.plan.workspace_bytes
-        r.ws = self.pool.take(wsb) if wsb else None
-
-    def _release(self, r, keep_outputs):
-        if not keep_outputs:
-            self.pool.give(r.out)
-        if r.ws is not None:
-            self.pool.give(r.ws)
-        r.ws = None
-
-    def _launch_single(self, r, stream):
-        import torch
-        r.plan(r.x, out=_view_like(r.out, r.x), stream=stream,
-               workspace=r.ws if r.ws is not None else None)
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(stream)
-        r.done_event = ev
-        self.stats["single_launches"] += 1
-
-    def _launch_group(self, group, stream):
-        import torch
-        from .batch import Batch
-        b = Batch([r.plan for r in group], [r.x for r in group],
-                  [_view_like(r.out, r.x) for r in group],
-                  workspace=None, stream=stream)
-        b(stream)
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(stream)
-        for r in group:
-            r.done_event = ev
-        self.stats["batched_launches"] += 1
-        return b
-
-    def run(self, requests, poll_s=20e-6, keep_outputs=False):
-        """Serve `requests` (sorted by arrival, seconds from start).  Returns
-        (finished requests with completion times, makespan in seconds).
-        With keep_outputs the output buffers stay with the requests instead of
-        returning to the pool."""
-        import torch
-        torch.cuda.synchronize(self.device)
-        start_ev = torch.cuda.Event(enable_timing=True)
-        start_ev.record(torch.cuda.current_stream(self.device))
-        torch.cuda.synchronize(self.device)
-        t0 = time.perf_counter()
-        pending = collections.deque(requests)
-        waiting = collections.deque()  # arrived, not admitted
-        # per stream, launches in issue order: (requests, event, batch or None);
-        # a stream completes its launches in order, so only heads are polled
-        queues = [collections.deque() for _ in self.streams]
-        used_bytes = 0
-        finished = []
-        while pending or waiting or any(queues):
-            now = time.perf_counter() - t0
-            while pending and pending[0].arrival <= now:
-                waiting.append(pending.popleft())
-            # retire
-            for q in queues:
-                while q and q[0][1].query():
-                    group, _, _ = q.popleft()
-                    for r in group:
-                        used_bytes -= r.bytes
-                        self._release(r, keep_outputs)
-                        finished.append(r)
-            # admit, in arrival order, while bytes and slots allow
-            admitted = []
-            while waiting:
-                r = waiting[0]
-                if r.plan is None:
-                    self._plan(r)
-                if used_bytes + r.bytes > self.budget and (used_bytes or admitted):
-                    break
-                waiting.popleft()
-                self._buffers(r)
-                used_bytes += r.bytes
-                admitted.append(r)
-            if admitted:
-                self.stats["admitted_rounds"] += 1
-                small = [r for r in admitted if (1 << r.n) * r.e <= self.batch_threshold]
-                large = [r for r in admitted if (1 << r.n) * r.e > self.batch_threshold]
-                work = [[r] for r in large]
-                if len(small) >= 2:
-                    work.append(small)
-                else:
-                    work.extend([r] for r in small)
-                for group in work:
-                    si = min(range(len(self.streams)), key=lambda i: len(queues[i]))
-                    stream = self.streams[si]
-                    keep = None
-                    if len(group) == 1:
-                        self._launch_single(group[0], stream)
-                    else:
-                        keep = self._launch_group(group, stream)
-                    queues[si].append((group, group[0].done_event, keep))
-                self.stats["max_in_flight_bytes"] = max(self.stats["max_in_flight_bytes"],
-                                                        used_bytes)
-                self.stats["max_in_flight"] = max(
-                    self.stats["max_in_flight"],
-                    sum(len(g) for q in queues for g, _, _ in q))
-            elif not any(queues) and not waiting and pending:
-                wait = pending[0].arrival - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 1e-3))
-            else:
-                time.sleep(poll_s)
-        torch.cuda.synchronize(self.device)
-        for r in finished:
-            r.completion = start_ev.elapsed_time(r.done_event) / 1e3
-        makespan = max(r.completion for r in finished)
-        return finished, makespan
-
-
-def serve_plain(requests, device, flags=B.BMMC_PLAN_PAPER, plan_cache=None,
-                keep_outputs=False):
-    """Baseline: in arrival order, one plan and one launch per request on a
-    single stream, no admission control, no batching.  Buffers of finished
-    requests are recycled unless keep_outputs."""
-    import torch
-    plans = plan_cache or PlanCache()
-    stream = torch.cuda.Stream(device=device)
-    pool = BufferPool(device)
-    torch.cuda.synchronize(device)
-    start_ev = torch.cuda.Event(enable_timing=True)
-    start_ev.record(torch.cuda.current_stream(device))
-    torch.cuda.synchronize(device)
-    t0 = time.perf_counter()
-    outs = []
-    live = collections.deque()
-    for r in requests:
-        wait = r.arrival - (time.perf_counter() - t0)
-        if wait > 0:
-            time.sleep(wait)
-        while live and live[0].done_event.query():
-            done = live.popleft()
-            if not keep_outputs:
-                pool.give(done.out)
-            if done.ws is not None:
-                pool.give(done.ws)
-            done.ws = None
-        r.plan = plans.get(r.n, r.rows, r.c, r.e, flags)
-        nb = (1 << r.n) * r.e
-        r.out = pool.take(nb)
-        wsb = r.plan.workspace_bytes
-        r.ws = pool.take(wsb) if wsb else None
-        r.plan(r.x, out=_view_like(r.out, r.x), stream=stream, workspace=r.ws)
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(stream)
-        r.done_event = ev
-        outs.append(r)
-        live.append(r)
-    torch.cuda.synchronize(device)
-    for r in outs:
-        r.completion = start_ev.elapsed_time(r.done_event) / 1e3
-    makespan = max(r.completion for r in outs)
-    return outs, makespan
-
-
-def _view_like(buf, like):
-    return buf.view(like.dtype).view(like.shape)
+            "mean_ms": sum(lat) / len(lat), "makespan_s": span_s,
+            "submit_late_p99_ms": _percentile(late, 0.99)}

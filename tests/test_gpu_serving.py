@@ -1,5 +1,6 @@
-"""Serving: every request's output is the same alone and in the mix, and the
-HBM admission budget holds."""
+"""Serving through the native server: every request's output is the same
+alone and in the mix, the HBM budget holds, and bad requests are refused at
+submission."""
 
 import numpy as np
 import pytest
@@ -17,7 +18,6 @@ def _inv(rows):
 
 
 def _requests(count, rate, n_lo, n_hi, seed=11):
-    import torch
     spec = wl.serving_requests(rate=rate, seconds=count / rate * 4, seed=seed,
                                n_lo=n_lo, n_hi=n_hi)[:count]
     reqs = []
@@ -32,43 +32,55 @@ def _requests(count, rate, n_lo, n_hi, seed=11):
     return reqs
 
 
+class _Raw:
+    """A device byte range as an array PyTorch can view without copying."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1",
+                                         "data": (ptr, False), "version": 3}
+
+
+def _output(r):
+    import torch
+    return torch.as_tensor(_Raw(r.out_ptr, (1 << r.n) * r.e), device="cuda")
+
+
 def _solo(r, flags):
     import torch
-    p = bm.Plan(r.n, r.rows, r.c, r.e, flags=flags)
-    y = p(r.x)
+    y = bm.Plan(r.n, r.rows, r.c, r.e, flags=flags)(r.x)
     torch.cuda.synchronize()
-    return y
+    return y.view(torch.uint8)
 
 
+@pytest.mark.parametrize("mode", ["continuous", "plain"])
 @pytest.mark.parametrize("flags", [bm.BMMC_PLAN_PAPER, bm.BMMC_PLAN_SINGLE_PASS])
-def test_results_same_alone_and_in_mix(flags):
+def test_results_same_alone_and_in_mix(mode, flags):
     import torch
     reqs = _requests(160, rate=20000.0, n_lo=12, n_hi=21)
-    srv = serving.Server(torch.device("cuda"), budget_bytes=200 << 20, streams=4,
-                         flags=flags, batch_threshold_bytes=1 << 20)
-    done, makespan = srv.run(reqs, keep_outputs=True)
-    assert len(done) == len(reqs) and makespan > 0
-    assert srv.stats["max_in_flight_bytes"] <= 200 << 20
-    assert srv.stats["batched_launches"] >= 1  # small requests were grouped
-    for r in done:
-        got = r.out.view(r.x.dtype).view(r.x.shape)
-        assert torch.equal(got, _solo(r, flags)), r.rid
-        assert r.completion >= r.arrival - 1e-3
-    # a sample against the oracle's definition too
-    for r in done[:20]:
+    budget = 200 << 20
+    srv = serving.Server("cuda", mode=mode, streams=4, budget_bytes=budget,
+                         arena_bytes=4 << 30, flags=flags, group_max_bytes=1 << 20,
+                         group_min=2, keep_outputs=True)
+    serving.drive(srv, reqs)
+    st = srv.stats()
+    assert st["completed"] == len(reqs)
+    biggest = max(2 * (1 << r.n) * r.e * 2 for r in reqs)
+    assert st["peak_bytes_in_flight"] <= max(budget, biggest)
+    if mode == "plain":
+        assert st["group_launches"] == 0 and st["streams"] == 1
+    for r in reqs:
+        assert r.status == bm.BMMC_OK
+        assert r.done_ms >= r.submit_ms
+        assert torch.equal(_output(r), _solo(r, flags)), r.rid
+    # a sample against the oracle's definition as well
+    for r in reqs[:16]:
         dest = f2.index_table(r.n, r.rows, r.c).astype(np.int64)
         xin = r.x.cpu().numpy().view(np.uint8).reshape(1 << r.n, r.e)
-        out = r.out.cpu().numpy().reshape(1 << r.n, r.e)
+        out = _output(r).cpu().numpy().reshape(1 << r.n, r.e)
         assert np.array_equal(out[dest], xin)
-
-
-def test_plain_loop_correct():
-    import torch
-    reqs = _requests(40, rate=5000.0, n_lo=12, n_hi=20, seed=12)
-    done, makespan = serving.serve_plain(reqs, torch.device("cuda"), keep_outputs=True)
-    for r in done:
-        got = r.out.view(r.x.dtype).view(r.x.shape)
-        assert torch.equal(got, _solo(r, bm.BMMC_PLAN_PAPER))
+    for r in reqs:
+        srv.release(r.out_ptr)
+    srv.close()
 
 
 def test_budget_blocks_admission():
@@ -77,10 +89,56 @@ def test_budget_blocks_admission():
     import torch
     reqs = _requests(12, rate=1e6, n_lo=22, n_hi=22, seed=13)
     one = max(2 * (1 << r.n) * r.e * 2 for r in reqs)
-    srv = serving.Server(torch.device("cuda"), budget_bytes=one, streams=4)
-    done, _ = srv.run(reqs, keep_outputs=True)
-    assert len(done) == 12
-    assert srv.stats["max_in_flight_bytes"] <= one
-    for r in done:
-        assert torch.equal(r.out.view(r.x.dtype).view(r.x.shape),
-                           _solo(r, bm.BMMC_PLAN_PAPER))
+    srv = serving.Server("cuda", budget_bytes=one, arena_bytes=2 << 30, streams=4,
+                         keep_outputs=True)
+    serving.drive(srv, reqs)
+    st = srv.stats()
+    assert st["completed"] == 12
+    assert st["peak_bytes_in_flight"] <= one
+    for r in reqs:
+        assert torch.equal(_output(r), _solo(r, bm.BMMC_PLAN_PAPER))
+        srv.release(r.out_ptr)
+    srv.close()
+
+
+@pytest.mark.parametrize("flags", [bm.BMMC_PLAN_PAPER, bm.BMMC_PLAN_SINGLE_PASS])
+def test_held_requests_are_grouped(flags):
+    """Requests that queue while admission is held are admitted in one round
+    on release and the small ones share one batch launch; the results are the
+    same as alone."""
+    import torch
+    reqs = _requests(24, rate=1e6, n_lo=12, n_hi=18, seed=21)
+    srv = serving.Server("cuda", budget_bytes=1 << 30, arena_bytes=1 << 30, flags=flags,
+                         group_max_bytes=1 << 22, group_min=2, keep_outputs=True)
+    srv.hold(True)
+    for r in reqs:
+        assert srv.submit(r.rid, r.n, r.rows, r.c, r.e, r.x) == bm.BMMC_OK
+    srv.hold(False)
+    srv.drain()
+    by_id = {rid: (st, out) for rid, st, _, _, out in srv.results()}
+    stats = srv.stats()
+    assert stats["group_launches"] == 1 and stats["grouped_requests"] == len(reqs)
+    for r in reqs:
+        st, r.out_ptr = by_id[r.rid]
+        assert st == bm.BMMC_OK
+        assert torch.equal(_output(r), _solo(r, flags))
+        srv.release(r.out_ptr)
+    srv.close()
+
+
+def test_submit_errors():
+    import torch
+    srv = serving.Server("cuda", budget_bytes=1 << 30, arena_bytes=64 << 20)
+    x = torch.zeros(1 << 20, dtype=torch.int32, device="cuda")
+    n = 20
+    singular = [1 << i for i in range(n - 1)] + [1]
+    assert srv.submit(1, n, singular, 0, 4, x) == bm.BMMC_ERR_SINGULAR
+    rows, c = wl.dense_bmmc(n, 1, _inv)  # output + workspace = 8 MiB: fits
+    assert srv.submit(2, n, rows, c, 4, x) == bm.BMMC_OK
+    big = torch.zeros(1 << 24, dtype=torch.int32, device="cuda")
+    rows24, c24 = wl.dense_bmmc(24, 1, _inv)  # 128 MiB > 64 MiB arena
+    assert srv.submit(3, 24, rows24, c24, 4, big) == bm.BMMC_ERR_TOO_LARGE
+    srv.drain()
+    res = srv.results()
+    assert [r[0] for r in res] == [2] and res[0][1] == bm.BMMC_OK
+    srv.close()

@@ -374,3 +374,76 @@ def test_factorisation_random(n, k):
         arr = np.arange(1 << n, dtype=np.uint32)
         two = oracle.apply(n, t1, c, oracle.apply(n, t2, 0, arr))
         assert np.array_equal(two, oracle.apply(n, rows, c, arr))
+
+
+# ---------------------------------------------------------------------------
+# parm and the sorting network (Sec. 6)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_parm_definition_equals_matrix_construction(n):
+    """Sec. 6.2's claim, parm m f = bmmc(A^-1, 0) o parm 2^(n-1) f o bmmc(A, 0),
+    checked against Sec. 6.1's definition for every mask, with an f that is
+    not symmetric in its input (it reverses and offsets)."""
+    def f(ys):
+        return [v * 10 + 1 for v in reversed(ys)]
+    half = 1 << (n - 1)
+    for mask in range(1, 1 << n):
+        xs = list(range(1 << n))
+        want = f2.parm_apply(mask, f, xs)
+        a = f2.parm_matrix(n, mask)
+        ia = f2.inverse(a, n)
+        y = list(f2.apply(n, a, 0, np.array(xs, dtype=np.int64)))
+        z = f(y[:half]) + f(y[half:])
+        got = list(f2.apply(n, ia, 0, np.array(z, dtype=np.int64)))
+        assert got == want, (n, mask)
+
+
+def test_parm_110_example_by_definition(golden):
+    """The sub-array / sub-index table of Sec. 6.2 through parm_apply: with f
+    the identity the array is unchanged, and with f tagging each sub-array the
+    tags land where the table says."""
+    g = golden["parm_110"]
+    mask = bits(g["mask"])
+    xs = list(range(8))
+    assert f2.parm_apply(mask, lambda ys: ys, xs) == xs
+    tags = f2.parm_apply(mask, lambda ys: [(len(ys), k) for k in range(len(ys))], xs)
+    for x, sub_array, sub_index in g["table"]:
+        assert tags[x][1] == sub_index
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_sorting_network_zero_one_principle(n):
+    """A comparator network sorts every input iff it sorts every 0-1 input;
+    all 2^(2^n) of them are checked."""
+    size = 1 << n
+    for v in range(1 << size):
+        xs = [(v >> i) & 1 for i in range(size)]
+        assert f2.sort_network(n, xs) == sorted(xs)
+
+
+@pytest.mark.parametrize("n", [5, 6, 7])
+def test_sorting_network_random(n):
+    g = wl.rng(n)
+    for _ in range(5):
+        xs = [int(v) for v in g.integers(-1000, 1000, size=1 << n)]
+        assert f2.sort_network(n, xs) == sorted(xs)
+
+
+def test_merge_needs_sorted_halves():
+    """merge n sorts an array whose even- and odd-indexed elements are each
+    sorted (Sec. 6.1), but not an arbitrary one."""
+    xs = [0, 1, 2, 3, 4, 5, 6, 7]
+    evens, odds = xs[0::2], xs[1::2]
+    inter = [None] * 8
+    inter[0::2] = sorted(odds)
+    inter[1::2] = sorted(evens)
+    assert f2.merge(3, inter) == sorted(xs)
+    # every 0-1 input with sorted even and odd halves is merged ...
+    for v in range(256):
+        ys = [(v >> i) & 1 for i in range(8)]
+        if ys[0::2] == sorted(ys[0::2]) and ys[1::2] == sorted(ys[1::2]):
+            assert f2.merge(3, ys) == sorted(ys)
+    # ... but some arbitrary input is not (merge alone is not a sorter)
+    assert any(f2.merge(3, [(v >> i) & 1 for i in range(8)])
+               != sorted((v >> i) & 1 for i in range(8)) for v in range(256))

@@ -26,7 +26,7 @@ def header_functions():
         if name.endswith(".h"):
             with open(os.path.join(ROOT, "include", name)) as f:
                 text += f.read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|size_t|const char \*)\s*\*?"
+    return sorted(set(re.findall(r"^\s*(?:int|void|size_t|double|const char \*)\s*\*?"
                                  r"(bmmc_\w+)\s*\(", text, re.M)))
 
 
