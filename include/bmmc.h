@@ -204,6 +204,27 @@ int bmmc_execute_ws(bmmc_plan p, const void *in, void *out, void *ws,
 int bmmc_execute_static_ws(bmmc_plan p, const void *in, void *out,
                            bmmc_stream_t stream);
 
+/* Key types for bmmc_execute_ce: how the bytes of an element compare. */
+enum bmmc_key_type {
+    BMMC_KEY_I32 = 1, BMMC_KEY_U32 = 2, BMMC_KEY_F32 = 3, /* 4-byte elements */
+    BMMC_KEY_I64 = 4, BMMC_KEY_U64 = 5, BMMC_KEY_F64 = 6  /* 8-byte elements */
+};
+
+/*
+ * A permutation followed by one column of comparators: out[A x + c] = in[x],
+ * and then every output pair (out[2j], out[2j + 1]) is left as it is when
+ * out[2j] <= out[2j + 1] under key_type and swapped otherwise -- the
+ * two-input V-column of the sorting network of Sec. 6.1 applied to adjacent
+ * elements.  The comparison runs in registers before the 16-byte store of
+ * the permutation's last pass, so a permute-then-compare step of a sorting
+ * network built from parm costs one pass.  Floating-point keys compare with
+ * IEEE <=, so a pair holding a NaN is swapped.
+ * ws: as for bmmc_execute_ws.  key_type must match elem_bytes (4 or 8).
+ * Errors: INVALID, UNSUPPORTED (element size or key), ALIAS, ALIGN, CUDA.
+ */
+int bmmc_execute_ce(bmmc_plan p, const void *in, void *out, void *ws, int key_type,
+                    bmmc_stream_t stream);
+
 /*
  * Host-side check of a plan's launch tables, with no GPU: walks the index
  * arithmetic of every pass for up to max_ctas thread blocks per pass (0 =

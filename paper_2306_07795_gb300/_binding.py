@@ -33,7 +33,7 @@ EXPORTED = (
     "bmmc_plan_inverse",
     "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws",
     "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
-    "bmmc_strerror", "bmmc_plan_compose", "bmmc_parm_matrix",
+    "bmmc_strerror", "bmmc_plan_compose", "bmmc_parm_matrix", "bmmc_execute_ce",
     # include/bmmc_batch.h
     "bmmc_batch_workspace_bytes", "bmmc_batch_table_bytes", "bmmc_batch_create",
     "bmmc_batch_execute",
@@ -113,6 +113,7 @@ def lib():
         "bmmc_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "bmmc_plan_compose": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
+        "bmmc_execute_ce": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, vp]),
         "bmmc_parm_matrix": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, u64p]),
         "bmmc_batch_workspace_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_table_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
@@ -239,6 +240,15 @@ def bmmc_plan_compose(second, first):
     out = ctypes.c_void_p()
     _check(lib().bmmc_plan_compose(second, first, ctypes.byref(out)), "bmmc_plan_compose")
     return out
+
+
+BMMC_KEY_I32, BMMC_KEY_U32, BMMC_KEY_F32 = 1, 2, 3
+BMMC_KEY_I64, BMMC_KEY_U64, BMMC_KEY_F64 = 4, 5, 6
+
+
+def bmmc_execute_ce(h, in_ptr, out_ptr, ws_ptr, key_type, stream=0):
+    _check(lib().bmmc_execute_ce(h, in_ptr, out_ptr, ws_ptr, key_type, stream),
+           "bmmc_execute_ce")
 
 
 def bmmc_parm_matrix(n, mask):

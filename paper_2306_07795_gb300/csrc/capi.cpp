@@ -13,7 +13,8 @@
 #include "plan_internal.hpp"
 
 namespace bmmc {
-cudaError_t launch_pass(const PassDesc &d, const void *in, void *out, cudaStream_t s);
+cudaError_t launch_pass(const PassDesc &d, const void *in, void *out, cudaStream_t s,
+                        int key);
 }
 
 using namespace bmmc;
@@ -112,21 +113,23 @@ int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
     return BMMC_OK;
 }
 
-int execute_impl(bmmc_plan p, const void *in, void *out, void *ws, cudaStream_t s)
+// key: comparator epilogue of the last pass (0 = none).
+int execute_impl(bmmc_plan p, const void *in, void *out, void *ws, cudaStream_t s,
+                 int key = 0)
 {
     const uint64_t bytes = array_bytes(p);
     if (((uintptr_t)in | (uintptr_t)out) & 15u) return BMMC_ERR_ALIGN;
     if (overlap(in, out, bytes)) return BMMC_ERR_ALIAS;
     if (p->npass == 1) {
-        cudaError_t err = launch_pass(p->desc[0], in, out, s);
+        cudaError_t err = launch_pass(p->desc[0], in, out, s, key);
         return err == cudaSuccess ? BMMC_OK : BMMC_ERR_CUDA;
     }
     if (!ws) return BMMC_ERR_INVALID;
     if ((uintptr_t)ws & 15u) return BMMC_ERR_ALIGN;
     if (overlap(ws, in, bytes) || overlap(ws, out, bytes)) return BMMC_ERR_ALIAS;
-    cudaError_t err = launch_pass(p->desc[0], in, ws, s);
+    cudaError_t err = launch_pass(p->desc[0], in, ws, s, 0);
     if (err != cudaSuccess) return BMMC_ERR_CUDA;
-    err = launch_pass(p->desc[1], ws, out, s);
+    err = launch_pass(p->desc[1], ws, out, s, key);
     return err == cudaSuccess ? BMMC_OK : BMMC_ERR_CUDA;
 }
 
@@ -253,6 +256,17 @@ int bmmc_execute_ws(bmmc_plan p, const void *in, void *out, void *ws, bmmc_strea
 {
     if (!p || !in || !out) return BMMC_ERR_INVALID;
     return execute_impl(p, in, out, ws, (cudaStream_t)stream);
+}
+
+int bmmc_execute_ce(bmmc_plan p, const void *in, void *out, void *ws, int key_type,
+                    bmmc_stream_t stream)
+{
+    if (!p || !in || !out) return BMMC_ERR_INVALID;
+    const bool ok4 = p->e_log == 2 && key_type >= BMMC_KEY_I32 && key_type <= BMMC_KEY_F32;
+    const bool ok8 = p->e_log == 3 && key_type >= BMMC_KEY_I64 && key_type <= BMMC_KEY_F64;
+    if (!ok4 && !ok8) return BMMC_ERR_UNSUPPORTED;
+    if (p->n < 1) return BMMC_ERR_UNSUPPORTED;
+    return execute_impl(p, in, out, ws, (cudaStream_t)stream, key_type);
 }
 
 int bmmc_plan_verify(bmmc_plan p, uint64_t max_ctas)

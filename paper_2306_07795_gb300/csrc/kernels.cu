@@ -3,6 +3,8 @@
 // One thread block moves 2^it tiles of one pass; the body (cp.async tile
 // load into swizzled shared memory, barrier, 16-byte gathers and stores) is
 // dev::run_tile in tile_body.cuh, shared with the persistent batch kernel.
+// KEY selects an optional comparator epilogue (a column of compare-exchanges
+// on output pairs, for sorting networks built from permutations).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,60 +16,80 @@ namespace bmmc {
 namespace {
 
 // Element size 2^E_LOG bytes; one block per thread-block index of the pass.
-template <int E_LOG>
+template <int E_LOG, int KEY>
 __global__ void __launch_bounds__(256)
     bmmc_tiled_pass(const __grid_constant__ PassDesc d,
                     const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    dev::run_tile<E_LOG>(d, blockIdx.x, in, out, sbase, true);
+    dev::run_tile<E_LOG, KEY>(d, blockIdx.x, in, out, sbase, true);
 }
 
 // Arrays under 1 KiB: one block, one thread per element, direct index map.
-template <int E_LOG>
+template <int E_LOG, int KEY>
 __global__ void bmmc_naive_pass(const __grid_constant__ PassDesc d,
                                 const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
-    dev::run_naive<E_LOG>(d, in, out);
+    dev::run_naive<E_LOG, KEY>(d, in, out);
 }
 
 constexpr int kMaxDevices = 64;
 constexpr int kSmemLimit = 128 * 1024;
-bool g_attr_set[kMaxDevices][3];
+bool g_attr_set[kMaxDevices][3][7];
 
-template <int E_LOG>
+template <int E_LOG, int KEY>
 cudaError_t launch_typed(const PassDesc &d, const void *in, void *out, cudaStream_t s)
 {
     const uint8_t *src = static_cast<const uint8_t *>(in);
     uint8_t *dst = static_cast<uint8_t *>(out);
     if (d.naive) {
-        bmmc_naive_pass<E_LOG><<<1, 1u << d.n, 0, s>>>(d, src, dst);
+        bmmc_naive_pass<E_LOG, KEY><<<1, 1u << d.n, 0, s>>>(d, src, dst);
         return cudaGetLastError();
     }
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    if (dev >= 0 && dev < kMaxDevices && !g_attr_set[dev][E_LOG - 2]) {
-        err = cudaFuncSetAttribute(bmmc_tiled_pass<E_LOG>,
+    if (dev >= 0 && dev < kMaxDevices && !g_attr_set[dev][E_LOG - 2][KEY]) {
+        err = cudaFuncSetAttribute(bmmc_tiled_pass<E_LOG, KEY>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
         if (err != cudaSuccess) return err;
-        g_attr_set[dev][E_LOG - 2] = true;
+        g_attr_set[dev][E_LOG - 2][KEY] = true;
     }
     dim3 grid(1u << d.n_cta);
     dim3 block(1u << d.thread_bits);
-    bmmc_tiled_pass<E_LOG><<<grid, block, d.smem_bytes, s>>>(d, src, dst);
+    bmmc_tiled_pass<E_LOG, KEY><<<grid, block, d.smem_bytes, s>>>(d, src, dst);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_pass(const PassDesc &d, const void *in, void *out, cudaStream_t s)
+// key: 0 (plain permutation) or a bmmc_key_type value matching the element
+// size (1..3 for 4-byte, 4..6 for 8-byte elements).
+cudaError_t launch_pass(const PassDesc &d, const void *in, void *out, cudaStream_t s,
+                        int key)
 {
+    using namespace dev;
     switch (d.e_log) {
-    case 2: return launch_typed<2>(d, in, out, s);
-    case 3: return launch_typed<3>(d, in, out, s);
-    case 4: return launch_typed<4>(d, in, out, s);
+    case 2:
+        switch (key) {
+        case kKeyNone: return launch_typed<2, kKeyNone>(d, in, out, s);
+        case kKeyI32: return launch_typed<2, kKeyI32>(d, in, out, s);
+        case kKeyU32: return launch_typed<2, kKeyU32>(d, in, out, s);
+        case kKeyF32: return launch_typed<2, kKeyF32>(d, in, out, s);
+        default: return cudaErrorInvalidValue;
+        }
+    case 3:
+        switch (key) {
+        case kKeyNone: return launch_typed<3, kKeyNone>(d, in, out, s);
+        case kKeyI64: return launch_typed<3, kKeyI64>(d, in, out, s);
+        case kKeyU64: return launch_typed<3, kKeyU64>(d, in, out, s);
+        case kKeyF64: return launch_typed<3, kKeyF64>(d, in, out, s);
+        default: return cudaErrorInvalidValue;
+        }
+    case 4:
+        if (key != kKeyNone) return cudaErrorInvalidValue;
+        return launch_typed<4, kKeyNone>(d, in, out, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -77,11 +77,54 @@ __device__ __forceinline__ void swap_if(bool c, T &a, T &b)
     b = tb;
 }
 
+// Key types of the compare-exchange epilogue (values of bmmc_key_type).
+constexpr int kKeyNone = 0, kKeyI32 = 1, kKeyU32 = 2, kKeyF32 = 3, kKeyI64 = 4,
+              kKeyU64 = 5, kKeyF64 = 6;
+
+// One comparator of a sorting network (Sec. 6.1, vcolumn 1): the pair stays
+// when a <= b and is swapped otherwise.
+template <int KEY>
+__device__ __forceinline__ bool keep_pair(uint32_t a, uint32_t b)
+{
+    if constexpr (KEY == kKeyI32) return (int32_t)a <= (int32_t)b;
+    else if constexpr (KEY == kKeyU32) return a <= b;
+    else return __uint_as_float(a) <= __uint_as_float(b);
+}
+
+template <int KEY>
+__device__ __forceinline__ bool keep_pair64(uint64_t a, uint64_t b)
+{
+    if constexpr (KEY == kKeyI64) return (int64_t)a <= (int64_t)b;
+    else if constexpr (KEY == kKeyU64) return a <= b;
+    else return __longlong_as_double((long long)a) <= __longlong_as_double((long long)b);
+}
+
+// Order the element pairs (2j, 2j+1) inside one 16-byte output chunk.
+template <int E_LOG, int KEY>
+__device__ __forceinline__ uint4 compare_exchange(uint4 v)
+{
+    if constexpr (KEY == kKeyNone) {
+        return v;
+    } else if constexpr (E_LOG == 2) {
+        const bool k0 = keep_pair<KEY>(v.x, v.y);
+        const bool k1 = keep_pair<KEY>(v.z, v.w);
+        swap_if(!k0, v.x, v.y);
+        swap_if(!k1, v.z, v.w);
+        return v;
+    } else {
+        const uint64_t a = ((uint64_t)v.y << 32) | v.x;
+        const uint64_t b = ((uint64_t)v.w << 32) | v.z;
+        if (keep_pair64<KEY>(a, b)) return v;
+        return make_uint4(v.z, v.w, v.x, v.y);
+    }
+}
+
 // One thread block of a tiled pass.  `active` is false for whole warps
 // beyond the pass's 2^thread_bits threads (batch kernel); those warps only
 // take part in the barrier.  sbase: shared-memory byte address of the tile
-// buffer (d.smem_bytes long, 128-byte aligned).
-template <int E_LOG>
+// buffer (d.smem_bytes long, 128-byte aligned).  KEY != kKeyNone orders each
+// output pair before the store (a comparator column of a sorting network).
+template <int E_LOG, int KEY = kKeyNone>
 __device__ __forceinline__ void run_tile(const PassDesc &d, uint32_t cta,
                                          const uint8_t *__restrict__ in,
                                          uint8_t *__restrict__ out, uint32_t sbase,
@@ -144,25 +187,48 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, uint32_t cta,
         } else {
             v = lds128(sbase + ((s ^ d.elem_src[0]) << 4));
         }
-        stg128(out + ((uint64_t)o << E_LOG), v);
+        stg128(out + ((uint64_t)o << E_LOG), compare_exchange<E_LOG, KEY>(v));
     }
 }
 
-// Arrays under 1 KiB: thread x < 2^n copies element x to T x + c.
-template <int E_LOG>
+// Arrays under 1 KiB: thread x < 2^n copies element x to T x + c (one
+// block).  With a KEY, the block then orders the output pairs in place.
+template <int E_LOG, int KEY = kKeyNone>
 __device__ __forceinline__ void run_naive(const PassDesc &d,
                                           const uint8_t *__restrict__ in,
                                           uint8_t *__restrict__ out)
 {
     const uint32_t x = threadIdx.x;
-    if (x >= (1u << d.n)) return;
-    const uint32_t y = bmmc_map(d.rows, d.n, d.c, x);
-    if constexpr (E_LOG == 2) {
-        reinterpret_cast<uint32_t *>(out)[y] = reinterpret_cast<const uint32_t *>(in)[x];
-    } else if constexpr (E_LOG == 3) {
-        reinterpret_cast<uint2 *>(out)[y] = reinterpret_cast<const uint2 *>(in)[x];
-    } else {
-        reinterpret_cast<uint4 *>(out)[y] = reinterpret_cast<const uint4 *>(in)[x];
+    const uint32_t count = 1u << d.n;
+    if (x < count) {
+        const uint32_t y = bmmc_map(d.rows, d.n, d.c, x);
+        if constexpr (E_LOG == 2) {
+            reinterpret_cast<uint32_t *>(out)[y] = reinterpret_cast<const uint32_t *>(in)[x];
+        } else if constexpr (E_LOG == 3) {
+            reinterpret_cast<uint2 *>(out)[y] = reinterpret_cast<const uint2 *>(in)[x];
+        } else {
+            reinterpret_cast<uint4 *>(out)[y] = reinterpret_cast<const uint4 *>(in)[x];
+        }
+    }
+    if constexpr (KEY != kKeyNone) {
+        __syncthreads();
+        if (x < count / 2) {
+            if constexpr (E_LOG == 2) {
+                uint32_t *o = reinterpret_cast<uint32_t *>(out);
+                uint32_t a = o[2 * x], b = o[2 * x + 1];
+                if (!keep_pair<KEY>(a, b)) {
+                    o[2 * x] = b;
+                    o[2 * x + 1] = a;
+                }
+            } else {
+                uint64_t *o = reinterpret_cast<uint64_t *>(out);
+                uint64_t a = o[2 * x], b = o[2 * x + 1];
+                if (!keep_pair64<KEY>(a, b)) {
+                    o[2 * x] = b;
+                    o[2 * x + 1] = a;
+                }
+            }
+        }
     }
 }
 

@@ -1,0 +1,167 @@
+"""The sorting network of Sec. 6.1, compiled to fused permute-and-compare passes.
+
+The paper writes an even/odd merge sort with a balanced periodic merger in
+terms of parm:
+
+    sort n    = merge n  o  parm 1 (sort (n - 1))
+    merge n   = parm 2^(n-1) (merge (n - 1))  o  vcolumn n
+    vcolumn n = parm 3 (vcolumn (n - 1)),   vcolumn 1 orders a pair
+
+and parm m f = bmmc(A^{-1}) o parm 2^(n-1) f o bmmc(A) (Sec. 6.2), where the
+inner f acts on the low n - 1 index bits (the two halves).  Unrolling the
+recursion gives a straight program of permutations and comparator columns;
+every comparator column compares adjacent pairs (index bit 0), because the
+innermost f is vcolumn 1 on two-element arrays.  The fusion rule (Sec. 3)
+collapses each run of permutations between two columns into one BMMC, so
+
+    sort n = P_final o CE o P_s o ... o CE o P_1
+
+with n (n + 1) / 2 comparator columns.  Each "CE o P" is one pass of the
+library (bmmc_execute_ce: the comparator runs in registers before the
+permutation's 16-byte store), and the whole network is a CUDA-graph-friendly
+sequence of single-pass launches.
+
+Host-side planning uses small F2 matrix products over row masks; the data
+path is entirely library kernels.
+"""
+
+from . import _binding as B
+from .plan import Plan
+
+_KEYS = {}
+
+
+def _key_for(dtype):
+    import torch
+    if not _KEYS:
+        _KEYS.update({torch.int32: (4, B.BMMC_KEY_I32), torch.float32: (4, B.BMMC_KEY_F32),
+                      torch.int64: (8, B.BMMC_KEY_I64), torch.float64: (8, B.BMMC_KEY_F64)})
+        if hasattr(torch, "uint32"):
+            _KEYS[torch.uint32] = (4, B.BMMC_KEY_U32)
+        if hasattr(torch, "uint64"):
+            _KEYS[torch.uint64] = (8, B.BMMC_KEY_U64)
+    if dtype not in _KEYS:
+        raise TypeError("sorting keys must be 32- or 64-bit integers or floats")
+    return _KEYS[dtype]
+
+
+# ---- host planning: programs of ("perm", rows) and ("ce",) over m bits -----
+
+def _mul(a, b):
+    """(a b) x = a (b x) over F2, matrices as row masks."""
+    out = []
+    for row in a:
+        acc = 0
+        j = 0
+        while row:
+            if row & 1:
+                acc ^= b[j]
+            row >>= 1
+            j += 1
+        out.append(acc)
+    return out
+
+
+def _identity(m):
+    return [1 << i for i in range(m)]
+
+
+def _inverse(rows):
+    m = len(rows)
+    p = Plan(m, rows, 0, 4, flags=B.BMMC_PLAN_SINGLE_PASS)
+    return B.bmmc_plan_matrix(B.bmmc_plan_inverse(p.handle), m)[0]
+
+
+def _lift(prog, m):
+    """A program on the low m bits, acting on m + 1 bits (top bit kept)."""
+    return [("perm", op[1] + [1 << m]) if op[0] == "perm" else op for op in prog]
+
+
+def _parm(mask, inner, n):
+    a = B.bmmc_parm_matrix(n, mask)
+    return [("perm", a)] + _lift(inner, n - 1) + [("perm", _inverse(a))]
+
+
+def _vcolumn(n):
+    return [("ce",)] if n == 1 else _parm(3, _vcolumn(n - 1), n)
+
+
+def _merge(n):
+    if n == 0:
+        return []
+    return _vcolumn(n) + _parm(1 << (n - 1), _merge(n - 1), n)
+
+
+def _sort(n):
+    if n == 0:
+        return []
+    return _parm(1, _sort(n - 1), n) + _merge(n)
+
+
+def schedule(n):
+    """The fused program of sort n: (stage matrices, final matrix).  Stage s
+    is 'permute by M_s, then order adjacent pairs'."""
+    stages = []
+    acc = _identity(n)
+    for op in _sort(n):
+        if op[0] == "perm":
+            acc = _mul(op[1], acc)
+        else:
+            stages.append(acc)
+            acc = _identity(n)
+    return stages, acc
+
+
+class SortingNetwork:
+    """Sorts the last dimension (2^n elements) of int32 / float32 / int64 /
+    float64 tensors with the network of Sec. 6.1; leading dimensions holding
+    2^b rows are sorted independently in the same passes."""
+
+    def __init__(self, n):
+        if n < 1 or n > 30:
+            raise ValueError("n must be in 1..30")
+        self.n = n
+        self.stage_rows, self.final_rows = schedule(n)
+        self._plans = {}
+
+    @property
+    def num_stages(self):
+        return len(self.stage_rows)
+
+    def _plans_for(self, elem_bytes, b):
+        key = (elem_bytes, b)
+        if key not in self._plans:
+            lift = [1 << (self.n + j) for j in range(b)]
+            mk = lambda rows: Plan(self.n + b, rows + lift, 0, elem_bytes,  # noqa: E731
+                                   flags=B.BMMC_PLAN_SINGLE_PASS)
+            stages = [mk(r) for r in self.stage_rows]
+            final = None if self.final_rows == _identity(self.n) else mk(self.final_rows)
+            self._plans[key] = (stages, final)
+        return self._plans[key]
+
+    def __call__(self, x, stream=None):
+        import torch
+        elem_bytes, key = _key_for(x.dtype)
+        if x.shape[-1] != 1 << self.n:
+            raise ValueError("last dimension must hold 2^n elements")
+        rows_total = x.numel() // x.shape[-1]
+        b = rows_total.bit_length() - 1
+        if rows_total != 1 << b:
+            raise ValueError("leading dimensions must hold a power-of-two count of rows")
+        stages, final = self._plans_for(elem_bytes, b)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        src = x.contiguous()
+        bufs = [torch.empty_like(src), torch.empty_like(src)]
+        cur = src
+        with torch.cuda.device(x.device):
+            for i, p in enumerate(stages):
+                dst = bufs[i & 1]
+                B.bmmc_execute_ce(p.handle, cur.data_ptr(), dst.data_ptr(), None, key,
+                                  stream.cuda_stream)
+                cur = dst
+            if final is not None:
+                dst = bufs[len(stages) & 1]
+                final(cur, out=dst, stream=stream)
+                cur = dst
+        return cur if cur is not src else src.clone()
