@@ -81,7 +81,10 @@ typedef struct bmmc_plan_options {
                             (the paper's n_tile); must satisfy
                             2^seg_bits * elem_bytes >= 128 */
     int cta_tile_log2;   /* log2 of the bytes one thread block moves */
-    int reserved[5];     /* must be zero */
+    int tile_order;      /* order of tiles over thread blocks: 1 = ascending
+                            input position, 2 = alternating input- and
+                            output-adjacent tiles; 0 = default (1) */
+    int reserved[4];     /* must be zero */
 } bmmc_plan_options;
 
 /*

@@ -71,8 +71,8 @@ class BmmcError(RuntimeError):
 
 class bmmc_plan_options(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("seg_bits", ctypes.c_int),
-                ("cta_tile_log2", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("cta_tile_log2", ctypes.c_int), ("tile_order", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -165,9 +165,9 @@ def bmmc_plan_create(n, rows, c, elem_bytes):
 
 
 def bmmc_plan_create_ex(n, rows, c, elem_bytes, flags=0, seg_bits=0,
-                        cta_tile_log2=0):
+                        cta_tile_log2=0, tile_order=0):
     h = ctypes.c_void_p()
-    o = bmmc_plan_options(flags, seg_bits, cta_tile_log2)
+    o = bmmc_plan_options(flags, seg_bits, cta_tile_log2, tile_order)
     _check(lib().bmmc_plan_create_ex(ctypes.byref(h), n, _rows(rows), c,
                                      elem_bytes, ctypes.byref(o)),
            "bmmc_plan_create_ex")

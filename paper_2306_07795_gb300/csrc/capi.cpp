@@ -60,6 +60,8 @@ int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
         opt.flags = opts->flags;
         opt.seg_bits = opts->seg_bits;
         opt.cta_tile_log2 = opts->cta_tile_log2;
+        opt.tile_order = opts->tile_order;
+        if (opt.tile_order < 0 || opt.tile_order > 2) return BMMC_ERR_UNSUPPORTED;
         if (opt.seg_bits && (opt.seg_bits < 7 - e_log || opt.seg_bits > 12))
             return BMMC_ERR_UNSUPPORTED;
         if (opt.cta_tile_log2 && (opt.cta_tile_log2 < 9 || opt.cta_tile_log2 > 17))
@@ -190,6 +192,7 @@ int bmmc_plan_inverse(bmmc_plan p, bmmc_plan *out)
     o.flags = p->opt.flags;
     o.seg_bits = p->opt.seg_bits;
     o.cta_tile_log2 = p->opt.cta_tile_log2;
+    o.tile_order = p->opt.tile_order;
     return create_impl(out, p->n, inv.r, inv.apply(p->c), (size_t)1 << p->e_log, &o);
 }
 
@@ -207,6 +210,7 @@ int bmmc_plan_compose(bmmc_plan second, bmmc_plan first, bmmc_plan *out)
     o.flags = second->opt.flags;
     o.seg_bits = second->opt.seg_bits;
     o.cta_tile_log2 = second->opt.cta_tile_log2;
+    o.tile_order = second->opt.tile_order;
     return create_impl(out, second->n, a.r, c, (size_t)1 << second->e_log, &o);
 }
 

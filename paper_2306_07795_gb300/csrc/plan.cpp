@@ -210,6 +210,36 @@ int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
     }
     if (ntb != n - k - m) return -3;
 
+    // Order of the tile-index bits.  Natural order (1): ascending input bit, so
+    // consecutive thread blocks read adjacent input segments.  Interleaved
+    // order (2): alternate the next input-adjacent bit with the next bit whose
+    // image moves the output by the smallest power of two, so that blocks
+    // running at the same time are local in the output as well.
+    if (opt.tile_order == 2 && ntb > 1) {
+        int outpos[64];
+        for (int j = 0; j < ntb; ++j) {
+            const uint64_t h = t.col(wb[j]) & ~lowmask;
+            outpos[j] = h ? __builtin_ctzll(h) : 64;
+        }
+        int by_out[64];
+        for (int j = 0; j < ntb; ++j) by_out[j] = j;
+        for (int a = 0; a < ntb; ++a)
+            for (int b = a + 1; b < ntb; ++b)
+                if (outpos[by_out[b]] < outpos[by_out[a]]) {
+                    int tmp = by_out[a]; by_out[a] = by_out[b]; by_out[b] = tmp;
+                }
+        bool used[64] = {};
+        int order[64];
+        int cnt = 0, ii = 0, io = 0;
+        while (cnt < ntb) {
+            while (ii < ntb && used[ii]) ++ii;
+            if (ii < ntb) { used[ii] = true; order[cnt++] = wb[ii]; }
+            while (io < ntb && used[by_out[io]]) ++io;
+            if (io < ntb && cnt < ntb) { used[by_out[io]] = true; order[cnt++] = wb[by_out[io]]; }
+        }
+        for (int j = 0; j < ntb; ++j) wb[j] = order[j];
+    }
+
     info->n_over = k - m;
     info->tiled = (f2::tiled_columns(t, k) != 0) ? 1 : 0;
 

@@ -15,6 +15,7 @@ struct PlanOptions {
     uint32_t flags = 0;     // 0 = paper (1 or 2 tiled passes), 1 = single pass
     int seg_bits = 0;       // 0 = default for the element size
     int cta_tile_log2 = 0;  // 0 = default (16 KiB per thread block)
+    int tile_order = 0;     // 0 = default, 1 = natural, 2 = interleaved
 };
 
 // Diagnostics of one pass, reported by bmmc_plan_describe.

@@ -12,7 +12,7 @@ class Plan:
     """
 
     def __init__(self, n, rows, c=0, elem_bytes=4, flags=B.BMMC_PLAN_PAPER,
-                 seg_bits=0, cta_tile_log2=0, _handle=None):
+                 seg_bits=0, cta_tile_log2=0, tile_order=0, _handle=None):
         self.n = int(n)
         self.rows = [int(r) for r in rows]
         self.c = int(c)
@@ -20,13 +20,15 @@ class Plan:
         self.flags = flags
         self.seg_bits = seg_bits
         self.cta_tile_log2 = cta_tile_log2
+        self.tile_order = tile_order
         if _handle is not None:
             self._h = _handle
         else:
             self._h = B.bmmc_plan_create_ex(self.n, self.rows, self.c,
                                             self.elem_bytes, flags, seg_bits,
-                                            cta_tile_log2)
+                                            cta_tile_log2, tile_order)
         self._inverse = None
+        self._ws_bytes = None
 
     # -- plan queries -------------------------------------------------------
     @property
@@ -62,7 +64,7 @@ class Plan:
             inv_rows, inv_c = B.bmmc_plan_matrix(h, self.n)
             self._inverse = Plan(self.n, inv_rows, inv_c, self.elem_bytes,
                                  self.flags, self.seg_bits, self.cta_tile_log2,
-                                 _handle=h)
+                                 self.tile_order, _handle=h)
         return self._inverse
 
     # -- execution ----------------------------------------------------------
@@ -83,20 +85,26 @@ class Plan:
         self._check_tensor(x, "x")
         if out is None:
             out = torch.empty_like(x)
-        self._check_tensor(out, "out")
+        else:
+            self._check_tensor(out, "out")
         dev = x.device
         if stream is None:
             stream = torch.cuda.current_stream(dev)
-        with torch.cuda.device(dev):
-            if self.workspace_bytes:
-                if workspace is None:
-                    workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8,
-                                            device=dev)
-                B.bmmc_execute_ws(self._h, x.data_ptr(), out.data_ptr(),
-                                  workspace.data_ptr(), stream.cuda_stream)
-            else:
-                B.bmmc_execute_ws(self._h, x.data_ptr(), out.data_ptr(), None,
-                                  stream.cuda_stream)
+        ws_bytes = self._ws_bytes
+        if ws_bytes is None:
+            ws_bytes = self._ws_bytes = self.workspace_bytes  # plans are immutable
+        if ws_bytes and workspace is None:
+            workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        ws_ptr = workspace.data_ptr() if ws_bytes else None
+        if dev.index == torch.cuda.current_device():
+            code = B.lib().bmmc_execute_ws(self._h, x.data_ptr(), out.data_ptr(), ws_ptr,
+                                           stream.cuda_stream)
+        else:
+            with torch.cuda.device(dev):
+                code = B.lib().bmmc_execute_ws(self._h, x.data_ptr(), out.data_ptr(),
+                                               ws_ptr, stream.cuda_stream)
+        if code != B.BMMC_OK:
+            raise B.BmmcError(code, "bmmc_execute_ws")
         return out
 
     def __del__(self):

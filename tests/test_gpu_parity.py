@@ -115,6 +115,15 @@ def test_tuning_options(e):
                                  cta_tile_log2=tile)
 
 
+@pytest.mark.parametrize("e", [4, 8, 16])
+def test_tile_order_alternating(e):
+    for n in (10, 18):
+        arr = wl.payload(n, e, seed=4)
+        for name, rows, c in classes(n, e, 40 + n):
+            for flags in (PAPER, SINGLE):
+                assert_exact(n, rows, c, e, arr, flags, tile_order=2)
+
+
 def test_float_payloads_bit_exact():
     """NaN payloads, -0.0, infinities and denormals move untouched."""
     n = 16

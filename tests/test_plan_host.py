@@ -166,6 +166,21 @@ def test_verify_tables_tuning_options(e):
                     assert p.verify() == 0, (seg, tile, i, p.describe())
 
 
+@pytest.mark.parametrize("e", [4, 8, 16])
+def test_verify_tables_tile_order(e):
+    """The alternating tile order only renumbers the thread blocks: every
+    pass must still cover each element exactly once."""
+    for n in (9, 15, 20):
+        for i, rows in enumerate(_workload_matrices(n, e, 11)):
+            for strategy in (0, 1):
+                for tile in (0, 12):
+                    p = bm.Plan(n, rows, wl.random_c(n, i), e, flags=strategy,
+                                cta_tile_log2=tile, tile_order=2)
+                    assert p.verify() == 0, (n, i, p.describe())
+    assert _create_code(10, wl.bit_reverse(10), 0, 4, tile_order=3) == \
+        bm.BMMC_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("n", [20, 24, 28, 32])
 def test_verify_tables_large_n_sampled(n):
     for e in (4, 8, 16):
