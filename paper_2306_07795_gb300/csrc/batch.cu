@@ -43,46 +43,98 @@ static_assert(sizeof(BatchEntry) == 32, "BatchEntry layout");
 constexpr uint32_t kDescSlot = (uint32_t)((sizeof(PassDesc) + 127) & ~(size_t)127);
 constexpr uint32_t kThreads = 256;
 
+// Shared memory: [table slot 0][table slot 1][tile buffer 0][tile buffer 1].
+// A block's items alternate between the slots: while one item is gathered and
+// stored from its buffer, the loads of the block's next item are already in
+// flight into the other buffer (cp.async groups).
 template <int E_LOG>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
     bmmc_batch_pass(const BatchEntry *__restrict__ ent, uint32_t count, uint64_t total,
-                    const uint8_t *__restrict__ descs)
+                    const uint8_t *__restrict__ descs, uint32_t tile_bytes)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    const PassDesc &sd = *reinterpret_cast<const PassDesc *>(smem);
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem) + kDescSlot;
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t tid = threadIdx.x;
 
-    const uint64_t begin = total * blockIdx.x / gridDim.x;
-    const uint64_t end = total * (blockIdx.x + 1) / gridDim.x;
-    if (begin >= end) return;
-    // last entry whose first item is <= begin
-    uint32_t lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (ent[mid].first_item <= begin) lo = mid;
-        else hi = mid - 1;
-    }
-    uint32_t a = lo;
-    uint32_t loaded = 0xffffffffu;
-    for (uint64_t item = begin; item < end; ++item) {
-        while (a + 1 < count && ent[a + 1].first_item <= item) ++a;
-        const BatchEntry en = ent[a];
-        if (en.desc != loaded) {
-            __syncthreads();  // every thread is done with the previous tables
-            const uint4 *src = reinterpret_cast<const uint4 *>(descs + (size_t)en.desc * kDescSlot);
-            uint4 *dst = reinterpret_cast<uint4 *>(smem);
-            for (uint32_t w = threadIdx.x; w < kDescSlot / 16; w += blockDim.x) dst[w] = src[w];
+    // Block b takes the contiguous range [b * per, (b + 1) * per) of the
+    // items.  (Striding over the items by the grid size measured 6% slower on
+    // a batch of 4096 arrays of 2^10..2^24 elements.)
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t begin = (uint64_t)blockIdx.x * per;
+    if (begin >= total) return;
+    const uint64_t end = begin + per < total ? begin + per : total;
+    uint32_t slot_table[2] = {0xffffffffu, 0xffffffffu};  // table held by each slot
+
+    // Advance *a to the last entry whose first item is <= item, by doubling
+    // steps and then bisection: O(log skipped) dependent loads, one for the
+    // next item of the same array.
+    auto find = [&](uint64_t item, uint32_t *a) {
+        uint32_t lo = *a, step = 1, hi;
+        for (;;) {
+            const uint32_t probe = lo + step;
+            if (probe >= count || ent[probe].first_item > item) {
+                hi = (probe < count ? probe : count) - 1;
+                break;
+            }
+            lo = probe;
+            step <<= 1;
+        }
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (ent[mid].first_item <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        *a = lo;
+    };
+    // Find the entry of `item` and make slot `slot` hold its tables.  The
+    // slot's previous user finished before the last barrier.
+    auto stage = [&](uint64_t item, int slot, uint32_t *a) {
+        find(item, a);
+        const uint32_t desc = ent[*a].desc;
+        if (desc != slot_table[slot]) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(descs + (size_t)desc * kDescSlot);
+            uint4 *dst = reinterpret_cast<uint4 *>(smem + slot * kDescSlot);
+            for (uint32_t w = tid; w < kDescSlot / 16; w += blockDim.x) dst[w] = src[w];
             __syncthreads();
-            loaded = en.desc;
+            slot_table[slot] = desc;
         }
-        if (sd.naive) {
-            dev::run_naive<E_LOG>(sd, en.src, en.dst);
+    };
+    auto table = [&](int slot) -> const PassDesc & {
+        return *reinterpret_cast<const PassDesc *>(smem + slot * kDescSlot);
+    };
+    auto buffer = [&](int slot) { return s0 + 2 * kDescSlot + (uint32_t)slot * tile_bytes; };
+    auto issue = [&](uint64_t item, uint32_t a, int slot) {
+        const PassDesc &d = table(slot);
+        if (!d.naive && tid < (1u << d.thread_bits)) {
+            const dev::TileAddr t = dev::tile_addr(d, (uint32_t)(item - ent[a].first_item));
+            dev::tile_load<E_LOG>(d, t, ent[a].src, buffer(slot));
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    uint32_t a_cur = 0;
+    stage(begin, 0, &a_cur);
+    issue(begin, a_cur, 0);
+    int slot = 0;
+    for (uint64_t item = begin; item < end; ++item, slot ^= 1) {
+        uint32_t a_next = a_cur;
+        if (item + 1 < end) {
+            stage(item + 1, slot ^ 1, &a_next);
+            issue(item + 1, a_next, slot ^ 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
-            const bool active = threadIdx.x < (1u << sd.thread_bits);
-            dev::run_tile<E_LOG>(sd, (uint32_t)(item - en.first_item), en.src, en.dst, sbase,
-                                 active);
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
-        __syncthreads();  // the tile buffer is reused by the next item
+        __syncthreads();  // every thread's copies of this item have landed
+        const PassDesc &d = table(slot);
+        if (d.naive) {
+            dev::run_naive<E_LOG>(d, ent[a_cur].src, ent[a_cur].dst);
+        } else if (tid < (1u << d.thread_bits)) {
+            const dev::TileAddr t = dev::tile_addr(d, (uint32_t)(item - ent[a_cur].first_item));
+            dev::tile_store<E_LOG, dev::kKeyNone>(d, t, ent[a_cur].dst, buffer(slot));
+        }
+        __syncthreads();  // buffer and table `slot` are free for the item after next
+        a_cur = a_next;
     }
 }
 
@@ -93,6 +145,7 @@ struct Group {
     uint64_t total = 0;
     size_t entry_offset = 0;  // byte offset of its entries in the device block
     uint32_t smem = 0;
+    uint32_t tile_bytes = 0;  // largest tile buffer of the group's passes
     uint32_t grid = 0;
     uint32_t arrays = 0;
 };
@@ -101,7 +154,8 @@ template <int E_LOG>
 cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
 {
     const BatchEntry *ent = reinterpret_cast<const BatchEntry *>(dmem + g.entry_offset);
-    bmmc_batch_pass<E_LOG><<<g.grid, kThreads, g.smem, s>>>(ent, g.count, g.total, dmem);
+    bmmc_batch_pass<E_LOG><<<g.grid, kThreads, g.smem, s>>>(ent, g.count, g.total, dmem,
+                                                           g.tile_bytes);
     return cudaGetLastError();
 }
 
@@ -265,7 +319,8 @@ int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
                 continue;
             }
             g.arrays = g.count;
-            g.smem = kDescSlot + max_smem;
+            g.tile_bytes = (max_smem + 127u) & ~127u;
+            g.smem = 2 * kDescSlot + 2 * g.tile_bytes;
             groups.push_back(g);
         }
     }

@@ -119,54 +119,61 @@ __device__ __forceinline__ uint4 compare_exchange(uint4 v)
     }
 }
 
-// One thread block of a tiled pass.  `active` is false for whole warps
-// beyond the pass's 2^thread_bits threads (batch kernel); those warps only
-// take part in the barrier.  sbase: shared-memory byte address of the tile
-// buffer (d.smem_bytes long, 128-byte aligned).  KEY != kKeyNone orders each
-// output pair before the store (a comparator column of a sorting network).
-template <int E_LOG, int KEY = kKeyNone>
-__device__ __forceinline__ void run_tile(const PassDesc &d, uint32_t cta,
-                                         const uint8_t *__restrict__ in,
-                                         uint8_t *__restrict__ out, uint32_t sbase,
-                                         bool active)
+// Per-thread parts of a block's addresses (see pass_desc.h::thread_base; the
+// block part is XOR-reduced across the warp: lane b contributes table entry
+// b when bit b of the block index is set).  Only for active warps.
+struct TileAddr {
+    uint32_t in, dst, src, out, rot;
+};
+
+__device__ __forceinline__ TileAddr tile_addr(const PassDesc &d, uint32_t cta)
 {
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31u;
-    uint32_t t_in = 0, t_dst = 0, t_src = 0, t_out = 0, rot = 0;
-    const uint32_t loop = d.loop;
-    if (active) {
-        // Thread-block part of every address: lane b contributes table entry
-        // b when bit b of the block index is set, and the warp XOR-reduces.
-        const bool bit = (lane < d.n_cta) && ((cta >> lane) & 1u);
-        t_in = __reduce_xor_sync(0xffffffffu, bit ? d.cta_in[lane] : 0u);
-        t_out = __reduce_xor_sync(0xffffffffu, bit ? d.cta_out[lane] : 0u) ^ d.out_const;
-        t_src = __reduce_xor_sync(0xffffffffu, bit ? d.cta_src[lane] : 0u) ^ d.src_const;
+    const bool bit = (lane < d.n_cta) && ((cta >> lane) & 1u);
+    TileAddr a;
+    a.in = __reduce_xor_sync(0xffffffffu, bit ? d.cta_in[lane] : 0u);
+    a.out = __reduce_xor_sync(0xffffffffu, bit ? d.cta_out[lane] : 0u) ^ d.out_const;
+    a.src = __reduce_xor_sync(0xffffffffu, bit ? d.cta_src[lane] : 0u) ^ d.src_const;
+    a.dst = 0u;
+    a.rot = 0u;
 #pragma unroll
-        for (int b = 0; b < kMaxThreadBits; ++b) {
-            if (b < (int)d.thread_bits && ((tid >> b) & 1u)) {
-                t_in ^= d.thr_in[b];
-                t_dst ^= d.thr_dst[b];
-                t_src ^= d.thr_src[b];
-                t_out ^= d.thr_out[b];
-                rot ^= d.thr_rot[b];
-            }
+    for (int b = 0; b < kMaxThreadBits; ++b) {
+        if (b < (int)d.thread_bits && ((tid >> b) & 1u)) {
+            a.in ^= d.thr_in[b];
+            a.dst ^= d.thr_dst[b];
+            a.src ^= d.thr_src[b];
+            a.out ^= d.thr_out[b];
+            a.rot ^= d.thr_rot[b];
         }
-        // Phase 1: input segments -> shared memory.
-        for (uint32_t i = 0; i < loop; ++i) {
-            const uint32_t g = t_in ^ d.loop_in[i];
-            const uint32_t s = t_dst ^ d.loop_dst[i];
-            cp_async_16(sbase + (s << E_LOG), in + ((uint64_t)g << E_LOG));
-        }
-        cp_async_wait_all();
     }
-    __syncthreads();
-    if (!active) return;
+    return a;
+}
 
-    // Phase 2: shared memory -> output chunks.
-    t_src ^= d.elem_src[rot];
+// Phase 1: this thread's input chunks -> shared memory (asynchronous).
+template <int E_LOG>
+__device__ __forceinline__ void tile_load(const PassDesc &d, const TileAddr &a,
+                                          const uint8_t *__restrict__ in, uint32_t sbase)
+{
+    const uint32_t loop = d.loop;
+    for (uint32_t i = 0; i < loop; ++i) {
+        const uint32_t g = a.in ^ d.loop_in[i];
+        const uint32_t s = a.dst ^ d.loop_dst[i];
+        cp_async_16(sbase + (s << E_LOG), in + ((uint64_t)g << E_LOG));
+    }
+}
+
+// Phase 2: shared memory -> this thread's output chunks.
+template <int E_LOG, int KEY>
+__device__ __forceinline__ void tile_store(const PassDesc &d, const TileAddr &a,
+                                           uint8_t *__restrict__ out, uint32_t sbase)
+{
+    const uint32_t loop = d.loop;
+    const uint32_t rot = a.rot;
+    const uint32_t t_src = a.src ^ d.elem_src[rot];
     for (uint32_t i = 0; i < loop; ++i) {
         const uint32_t s = t_src ^ d.loop_src[i];
-        const uint32_t o = t_out ^ d.loop_out[i];
+        const uint32_t o = a.out ^ d.loop_out[i];
         uint4 v;
         if constexpr (E_LOG == 2) {
             uint32_t a0 = lds32(sbase + ((s ^ d.elem_src[0]) << 2));
@@ -189,6 +196,27 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, uint32_t cta,
         }
         stg128(out + ((uint64_t)o << E_LOG), compare_exchange<E_LOG, KEY>(v));
     }
+}
+
+// One thread block of a tiled pass.  `active` is false for whole warps
+// beyond the pass's 2^thread_bits threads (batch kernel); those warps only
+// take part in the barrier.  sbase: shared-memory byte address of the tile
+// buffer (d.smem_bytes long, 128-byte aligned).  KEY != kKeyNone orders each
+// output pair before the store (a comparator column of a sorting network).
+template <int E_LOG, int KEY = kKeyNone>
+__device__ __forceinline__ void run_tile(const PassDesc &d, uint32_t cta,
+                                         const uint8_t *__restrict__ in,
+                                         uint8_t *__restrict__ out, uint32_t sbase,
+                                         bool active)
+{
+    TileAddr a;
+    if (active) {
+        a = tile_addr(d, cta);
+        tile_load<E_LOG>(d, a, in, sbase);
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    if (active) tile_store<E_LOG, KEY>(d, a, out, sbase);
 }
 
 // Arrays under 1 KiB: thread x < 2^n copies element x to T x + c (one
