@@ -139,6 +139,19 @@ class SortingNetwork:
             self._plans[key] = (stages, final)
         return self._plans[key]
 
+    def capture(self, x):
+        """Record the whole network for input buffer x in a CUDA graph.
+        Returns (graph, out): after graph.replay(), out holds x sorted (x may be
+        refilled between replays; its address is baked into the graph)."""
+        import torch
+        self(x)  # plans and kernel attributes outside capture
+        torch.cuda.synchronize(x.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.device(x.device):
+            with torch.cuda.graph(g):
+                out = self(x)
+        return g, out
+
     def __call__(self, x, stream=None):
         import torch
         elem_bytes, key = _key_for(x.dtype)

@@ -103,3 +103,17 @@ def test_sorting_network_rows_and_oracle_recursion():
     for r in range(8):
         xs = x[r].cpu().tolist()
         assert got[r].cpu().tolist() == f2.sort_network(n, xs)
+
+
+def test_sorting_network_graph_replay():
+    import torch
+    n = 14
+    net = SortingNetwork(n)
+    x = torch.randn(1 << n, device="cuda")
+    graph, out = net.capture(x)
+    for seed in range(3):
+        x.copy_(torch.randn(1 << n, device="cuda", generator=torch.Generator(
+            device="cuda").manual_seed(seed)))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, torch.sort(x).values)
