@@ -884,14 +884,47 @@ def main():
         s_out.wait_stream(s_run)
         b.record(s_out)
         torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+
+        # The host link alone: the same copies in the same stream pattern with
+        # no kernel (the D2H copy reads back the buffer the H2D copy filled).
+        # This is the ceiling of the end-to-end number.
+        def link_step():
+            for i, (cls, e, rows, c) in enumerate(items):
+                k = (e, i & 1)
+                x, y, ws = sets[e][i & 1]
+                hin, hout = host[e]
+                if k in done_out:
+                    s_in.wait_event(done_out[k])
+                with torch.cuda.stream(s_in):
+                    x.copy_(hin, non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+                s_out.wait_event(ev_in)
+                with torch.cuda.stream(s_out):
+                    hout.copy_(x, non_blocking=True)
+                ev_out = torch.cuda.Event()
+                ev_out.record(s_out)
+                done_out[k] = ev_out
+        done_out.clear()
+        a.record(s_in)
+        link_step()
+        s_out.wait_stream(s_in)
+        b.record(s_out)
+        torch.cuda.synchronize(dev)
+        link_ms = a.elapsed_time(b)
         del sets
         barrier(world)
-        ms = allreduce_max(world, a.elapsed_time(b))
+        ms = allreduce_max(world, ms)
+        link_ms = allreduce_max(world, link_ms)
         e2e_bytes = allreduce_sum(world, float(bytes_per_step * args.e2e_steps))
         hbytes = sum(N * e for (_, e, _, _) in items)
+        link_gbs = bytes_per_step * world / (link_ms / 1e3) / 1e9
         e2e = {"value": round(e2e_bytes / (ms / 1e3) / 1e9, 1), "unit": "GB/s",
                "h2d_bytes_per_step": hbytes, "d2h_bytes_per_step": hbytes,
-               "steps": args.e2e_steps, "warmup": 1}
+               "steps": args.e2e_steps, "warmup": 1,
+               "copies_only_gbs": round(link_gbs, 1),
+               "frac_of_copies_only": round(e2e_bytes / (ms / 1e3) / 1e9 / link_gbs, 4)}
         del host
 
     del bufs

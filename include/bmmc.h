@@ -57,7 +57,8 @@ enum bmmc_status {
     BMMC_ERR_ALIGN = -5,       /* a device pointer is not 16-byte aligned */
     BMMC_ERR_OOM = -6,         /* device or host allocation failed */
     BMMC_ERR_CUDA = -7,        /* a CUDA runtime call or launch failed */
-    BMMC_ERR_TOO_LARGE = -8    /* workspace needed exceeds the static scratch */
+    BMMC_ERR_TOO_LARGE = -8    /* a size limit of the entry point: the static
+                                  scratch, or a batch phase of 2^32 tiles */
 };
 
 /* Planning strategies (bmmc_plan_options.flags). */

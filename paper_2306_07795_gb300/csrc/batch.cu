@@ -49,7 +49,7 @@ constexpr uint32_t kThreads = 256;
 // flight into the other buffer (cp.async groups).
 template <int E_LOG>
 __global__ void __launch_bounds__(kThreads, 5)
-    bmmc_batch_pass(const BatchEntry *__restrict__ ent, uint32_t count, uint64_t total,
+    bmmc_batch_pass(const BatchEntry *__restrict__ ent, uint32_t count, uint32_t total,
                     const uint8_t *__restrict__ descs, uint32_t tile_bytes)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -59,16 +59,16 @@ __global__ void __launch_bounds__(kThreads, 5)
     // Block b takes the contiguous range [b * per, (b + 1) * per) of the
     // items.  (Striding over the items by the grid size measured 6% slower on
     // a batch of 4096 arrays of 2^10..2^24 elements.)
-    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
-    const uint64_t begin = (uint64_t)blockIdx.x * per;
+    const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint32_t begin = blockIdx.x * per;
     if (begin >= total) return;
-    const uint64_t end = begin + per < total ? begin + per : total;
-    uint32_t slot_table[2] = {0xffffffffu, 0xffffffffu};  // table held by each slot
+    const uint32_t end = total - begin > per ? begin + per : total;
+    uint32_t held0 = 0xffffffffu, held1 = 0xffffffffu;  // table held by each slot
 
     // Advance *a to the last entry whose first item is <= item, by doubling
     // steps and then bisection: O(log skipped) dependent loads, one for the
     // next item of the same array.
-    auto find = [&](uint64_t item, uint32_t *a) {
+    auto find = [&](uint32_t item, uint32_t *a) {
         uint32_t lo = *a, step = 1, hi;
         for (;;) {
             const uint32_t probe = lo + step;
@@ -88,27 +88,37 @@ __global__ void __launch_bounds__(kThreads, 5)
     };
     // Find the entry of `item` and make slot `slot` hold its tables.  The
     // slot's previous user finished before the last barrier.
-    auto stage = [&](uint64_t item, int slot, uint32_t *a) {
+    auto stage = [&](uint32_t item, int slot, uint32_t *a) {
         find(item, a);
         const uint32_t desc = ent[*a].desc;
-        if (desc != slot_table[slot]) {
+        if (desc != (slot ? held1 : held0)) {
             const uint4 *src = reinterpret_cast<const uint4 *>(descs + (size_t)desc * kDescSlot);
             uint4 *dst = reinterpret_cast<uint4 *>(smem + slot * kDescSlot);
             for (uint32_t w = tid; w < kDescSlot / 16; w += blockDim.x) dst[w] = src[w];
             __syncthreads();
-            slot_table[slot] = desc;
+            if (slot) held1 = desc;
+            else held0 = desc;
         }
     };
     auto table = [&](int slot) -> const PassDesc & {
         return *reinterpret_cast<const PassDesc *>(smem + slot * kDescSlot);
     };
     auto buffer = [&](int slot) { return s0 + 2 * kDescSlot + (uint32_t)slot * tile_bytes; };
-    auto issue = [&](uint64_t item, uint32_t a, int slot) {
-        const PassDesc &d = table(slot);
-        if (!d.naive && tid < (1u << d.thread_bits)) {
-            const dev::TileAddr t = dev::tile_addr(d, (uint32_t)(item - ent[a].first_item));
-            dev::tile_load<E_LOG>(d, t, ent[a].src, buffer(slot));
+    // Thread part of the addresses of the pass last seen (consecutive items
+    // of a block almost always belong to the same pass).
+    uint32_t tp_desc = 0xffffffffu;
+    dev::TileAddr tp;
+    auto addr = [&](const PassDesc &d, uint32_t a, uint32_t item) {
+        if (ent[a].desc != tp_desc) {
+            tp = dev::thread_part(d);
+            tp_desc = ent[a].desc;
         }
+        return dev::with_block(d, tp, item - (uint32_t)ent[a].first_item);
+    };
+    auto issue = [&](uint32_t item, uint32_t a, int slot) {
+        const PassDesc &d = table(slot);
+        if (!d.naive && tid < (1u << d.thread_bits))
+            dev::tile_load<E_LOG>(d, addr(d, a, item), ent[a].src, buffer(slot));
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
@@ -116,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 5)
     stage(begin, 0, &a_cur);
     issue(begin, a_cur, 0);
     int slot = 0;
-    for (uint64_t item = begin; item < end; ++item, slot ^= 1) {
+    for (uint32_t item = begin; item < end; ++item, slot ^= 1) {
         uint32_t a_next = a_cur;
         if (item + 1 < end) {
             stage(item + 1, slot ^ 1, &a_next);
@@ -130,8 +140,8 @@ __global__ void __launch_bounds__(kThreads, 5)
         if (d.naive) {
             dev::run_naive<E_LOG>(d, ent[a_cur].src, ent[a_cur].dst);
         } else if (tid < (1u << d.thread_bits)) {
-            const dev::TileAddr t = dev::tile_addr(d, (uint32_t)(item - ent[a_cur].first_item));
-            dev::tile_store<E_LOG, dev::kKeyNone>(d, t, ent[a_cur].dst, buffer(slot));
+            dev::tile_store<E_LOG, dev::kKeyNone>(d, addr(d, a_cur, item), ent[a_cur].dst,
+                                                  buffer(slot));
         }
         __syncthreads();  // buffer and table `slot` are free for the item after next
         a_cur = a_next;
@@ -154,7 +164,8 @@ template <int E_LOG>
 cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
 {
     const BatchEntry *ent = reinterpret_cast<const BatchEntry *>(dmem + g.entry_offset);
-    bmmc_batch_pass<E_LOG><<<g.grid, kThreads, g.smem, s>>>(ent, g.count, g.total, dmem,
+    bmmc_batch_pass<E_LOG><<<g.grid, kThreads, g.smem, s>>>(ent, g.count,
+                                                           (uint32_t)g.total, dmem,
                                                            g.tile_bytes);
     return cudaGetLastError();
 }
@@ -318,6 +329,9 @@ int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
                 entries.resize(g.entry_offset / sizeof(BatchEntry));
                 continue;
             }
+            // the kernel counts items in 32 bits (2^32 items of >= 512 bytes
+            // would exceed any device memory)
+            if (g.total > 0xffffffffull) return BMMC_ERR_TOO_LARGE;
             g.arrays = g.count;
             g.tile_bytes = (max_smem + 127u) & ~127u;
             g.smem = 2 * kDescSlot + 2 * g.tile_bytes;

@@ -344,7 +344,7 @@ const char *bmmc_strerror(int code)
     case BMMC_ERR_ALIGN: return "device pointer not 16-byte aligned";
     case BMMC_ERR_OOM: return "out of memory";
     case BMMC_ERR_CUDA: return "CUDA error";
-    case BMMC_ERR_TOO_LARGE: return "workspace exceeds the static scratch array";
+    case BMMC_ERR_TOO_LARGE: return "size limit exceeded (static scratch, or batch tiles)";
     default: return "unknown status";
     }
 }

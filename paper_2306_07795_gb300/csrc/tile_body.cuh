@@ -61,11 +61,14 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr)
     return v;
 }
 
+// No "memory" clobber: nothing in a pass reads what it stores, and the
+// barriers that order a block's work are compiler barriers themselves.
+// Without the clobber the compiler keeps table entries in registers across
+// the stores instead of reloading them every chunk.
 __device__ __forceinline__ void stg128(void *ptr, uint4 v)
 {
     asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"l"(ptr), "r"(v.x),
-                 "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
+                 "r"(v.y), "r"(v.z), "r"(v.w));
 }
 
 template <typename T>
@@ -126,17 +129,12 @@ struct TileAddr {
     uint32_t in, dst, src, out, rot;
 };
 
-__device__ __forceinline__ TileAddr tile_addr(const PassDesc &d, uint32_t cta)
+// The thread-index part: the same for every block of a pass, so a
+// persistent block computes it once per pass, not once per tile.
+__device__ __forceinline__ TileAddr thread_part(const PassDesc &d)
 {
     const uint32_t tid = threadIdx.x;
-    const uint32_t lane = tid & 31u;
-    const bool bit = (lane < d.n_cta) && ((cta >> lane) & 1u);
-    TileAddr a;
-    a.in = __reduce_xor_sync(0xffffffffu, bit ? d.cta_in[lane] : 0u);
-    a.out = __reduce_xor_sync(0xffffffffu, bit ? d.cta_out[lane] : 0u) ^ d.out_const;
-    a.src = __reduce_xor_sync(0xffffffffu, bit ? d.cta_src[lane] : 0u) ^ d.src_const;
-    a.dst = 0u;
-    a.rot = 0u;
+    TileAddr a = {0u, 0u, 0u, 0u, 0u};
 #pragma unroll
     for (int b = 0; b < kMaxThreadBits; ++b) {
         if (b < (int)d.thread_bits && ((tid >> b) & 1u)) {
@@ -148,6 +146,22 @@ __device__ __forceinline__ TileAddr tile_addr(const PassDesc &d, uint32_t cta)
         }
     }
     return a;
+}
+
+// Add the block-index part (and the complement vector) to a thread part.
+__device__ __forceinline__ TileAddr with_block(const PassDesc &d, TileAddr a, uint32_t cta)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const bool bit = (lane < d.n_cta) && ((cta >> lane) & 1u);
+    a.in ^= __reduce_xor_sync(0xffffffffu, bit ? d.cta_in[lane] : 0u);
+    a.out ^= __reduce_xor_sync(0xffffffffu, bit ? d.cta_out[lane] : 0u) ^ d.out_const;
+    a.src ^= __reduce_xor_sync(0xffffffffu, bit ? d.cta_src[lane] : 0u) ^ d.src_const;
+    return a;
+}
+
+__device__ __forceinline__ TileAddr tile_addr(const PassDesc &d, uint32_t cta)
+{
+    return with_block(d, thread_part(d), cta);
 }
 
 // Phase 1: this thread's input chunks -> shared memory (asynchronous).
@@ -171,15 +185,18 @@ __device__ __forceinline__ void tile_store(const PassDesc &d, const TileAddr &a,
     const uint32_t loop = d.loop;
     const uint32_t rot = a.rot;
     const uint32_t t_src = a.src ^ d.elem_src[rot];
+    // element offsets in registers for the whole loop
+    const uint32_t e1 = d.elem_src[1], e2 = d.elem_src[2], e3 = d.elem_src[3];
+    const uint32_t e0 = d.elem_src[0];
     for (uint32_t i = 0; i < loop; ++i) {
         const uint32_t s = t_src ^ d.loop_src[i];
         const uint32_t o = a.out ^ d.loop_out[i];
         uint4 v;
         if constexpr (E_LOG == 2) {
-            uint32_t a0 = lds32(sbase + ((s ^ d.elem_src[0]) << 2));
-            uint32_t a1 = lds32(sbase + ((s ^ d.elem_src[1]) << 2));
-            uint32_t a2 = lds32(sbase + ((s ^ d.elem_src[2]) << 2));
-            uint32_t a3 = lds32(sbase + ((s ^ d.elem_src[3]) << 2));
+            uint32_t a0 = lds32(sbase + ((s ^ e0) << 2));
+            uint32_t a1 = lds32(sbase + ((s ^ e1) << 2));
+            uint32_t a2 = lds32(sbase + ((s ^ e2) << 2));
+            uint32_t a3 = lds32(sbase + ((s ^ e3) << 2));
             // the value loaded by instruction j belongs to element j ^ rot
             swap_if((rot & 1u) != 0u, a0, a1);
             swap_if((rot & 1u) != 0u, a2, a3);
@@ -187,12 +204,12 @@ __device__ __forceinline__ void tile_store(const PassDesc &d, const TileAddr &a,
             swap_if((rot & 2u) != 0u, a1, a3);
             v = make_uint4(a0, a1, a2, a3);
         } else if constexpr (E_LOG == 3) {
-            uint2 a0 = lds64(sbase + ((s ^ d.elem_src[0]) << 3));
-            uint2 a1 = lds64(sbase + ((s ^ d.elem_src[1]) << 3));
+            uint2 a0 = lds64(sbase + ((s ^ e0) << 3));
+            uint2 a1 = lds64(sbase + ((s ^ e1) << 3));
             swap_if((rot & 1u) != 0u, a0, a1);
             v = make_uint4(a0.x, a0.y, a1.x, a1.y);
         } else {
-            v = lds128(sbase + ((s ^ d.elem_src[0]) << 4));
+            v = lds128(sbase + ((s ^ e0) << 4));
         }
         stg128(out + ((uint64_t)o << E_LOG), compare_exchange<E_LOG, KEY>(v));
     }
