@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    dev::run_tile<E_LOG, KEY>(d, blockIdx.x, in, out, sbase, true);
+    dev::run_tile<E_LOG, KEY>(d, blockIdx.x, in, out, sbase);
 }
 
 // Arrays under 1 KiB: one block, one thread per element, direct index map.
@@ -31,6 +31,8 @@ template <int E_LOG, int KEY>
 __global__ void bmmc_naive_pass(const __grid_constant__ PassDesc d,
                                 const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
+    dev::grid_dependency_wait();
+    dev::allow_dependent_launch();
     dev::run_naive<E_LOG, KEY>(d, in, out);
 }
 
@@ -38,15 +40,34 @@ constexpr int kMaxDevices = 64;
 constexpr int kSmemLimit = 128 * 1024;
 bool g_attr_set[kMaxDevices][3][7];
 
+// Every launch allows programmatic dependent launch: the kernels wait on the
+// grid dependency before their first global memory access, so a pass may be
+// scheduled while the previous kernel of the stream drains.
+template <typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int E_LOG, int KEY>
 cudaError_t launch_typed(const PassDesc &d, const void *in, void *out, cudaStream_t s)
 {
     const uint8_t *src = static_cast<const uint8_t *>(in);
     uint8_t *dst = static_cast<uint8_t *>(out);
-    if (d.naive) {
-        bmmc_naive_pass<E_LOG, KEY><<<1, 1u << d.n, 0, s>>>(d, src, dst);
-        return cudaGetLastError();
-    }
+    if (d.naive)
+        return launch_pdl(bmmc_naive_pass<E_LOG, KEY>, dim3(1), dim3(1u << d.n), 0, s, d, src,
+                          dst);
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
@@ -56,10 +77,8 @@ cudaError_t launch_typed(const PassDesc &d, const void *in, void *out, cudaStrea
         if (err != cudaSuccess) return err;
         g_attr_set[dev][E_LOG - 2][KEY] = true;
     }
-    dim3 grid(1u << d.n_cta);
-    dim3 block(1u << d.thread_bits);
-    bmmc_tiled_pass<E_LOG, KEY><<<grid, block, d.smem_bytes, s>>>(d, src, dst);
-    return cudaGetLastError();
+    return launch_pdl(bmmc_tiled_pass<E_LOG, KEY>, dim3(1u << d.n_cta),
+                      dim3(1u << d.thread_bits), d.smem_bytes, s, d, src, dst);
 }
 
 }  // namespace

@@ -31,6 +31,23 @@ __device__ __forceinline__ void cp_async_16(uint32_t smem_addr, const void *gptr
                  : "memory");
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may be scheduled while the previous kernel of its stream is
+// still finishing.  grid_dependency_wait() returns once that kernel has
+// completed and its writes are visible, so code before it may read kernel
+// parameters only.  allow_dependent_launch() lets the next such kernel be
+// scheduled once every block of this grid has issued it (it then still waits
+// for this grid to finish before touching memory).
+__device__ __forceinline__ void grid_dependency_wait()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void allow_dependent_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -215,25 +232,27 @@ __device__ __forceinline__ void tile_store(const PassDesc &d, const TileAddr &a,
     }
 }
 
-// One thread block of a tiled pass.  `active` is false for whole warps
-// beyond the pass's 2^thread_bits threads (batch kernel); those warps only
-// take part in the barrier.  sbase: shared-memory byte address of the tile
-// buffer (d.smem_bytes long, 128-byte aligned).  KEY != kKeyNone orders each
-// output pair before the store (a comparator column of a sorting network).
+// One thread block of a tiled pass launched on its own (one block per
+// thread-block index, every thread active).  The addresses are computed from
+// the parameters before the grid dependency wait, overlapping the previous
+// kernel's tail.  The next kernel may be scheduled only after the wait, so
+// at most one grid waits behind a running one (allowing it at entry let a
+// whole chain of captured passes pile up on the SMs and ran slower).
+// sbase: shared-memory byte address of the tile buffer (d.smem_bytes long,
+// 128-byte aligned).  KEY != kKeyNone orders each output pair before the
+// store (a comparator column of a sorting network).
 template <int E_LOG, int KEY = kKeyNone>
 __device__ __forceinline__ void run_tile(const PassDesc &d, uint32_t cta,
                                          const uint8_t *__restrict__ in,
-                                         uint8_t *__restrict__ out, uint32_t sbase,
-                                         bool active)
+                                         uint8_t *__restrict__ out, uint32_t sbase)
 {
-    TileAddr a;
-    if (active) {
-        a = tile_addr(d, cta);
-        tile_load<E_LOG>(d, a, in, sbase);
-        cp_async_wait_all();
-    }
+    const TileAddr a = tile_addr(d, cta);
+    grid_dependency_wait();
+    allow_dependent_launch();
+    tile_load<E_LOG>(d, a, in, sbase);
+    cp_async_wait_all();
     __syncthreads();
-    if (active) tile_store<E_LOG, KEY>(d, a, out, sbase);
+    tile_store<E_LOG, KEY>(d, a, out, sbase);
 }
 
 // Arrays under 1 KiB: thread x < 2^n copies element x to T x + c (one
