@@ -503,6 +503,17 @@ def bench_autograd(dev, iters=20):
         ms = a.elapsed_time(b) / iters
         out[name] = {"fwd_bwd_ms": round(ms, 4),
                      "gbs": round(2 * 2 * nbytes / (ms / 1e3) / 1e9, 1)}
+        # the same step captured in a CUDA graph (no Python or autograd-engine
+        # time between the launches)
+        x.grad = None
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            bmmc_permute(x, plan).backward(w)
+        gms = _time_ms(graph.replay, dev, iters)
+        out[name]["graph_fwd_bwd_ms"] = round(gms, 4)
+        out[name]["graph_gbs"] = round(2 * 2 * nbytes / (gms / 1e3) / 1e9, 1)
+        del graph
+        x.grad = None
     y = torch.empty_like(w)
     y.copy_(w)
     a = torch.cuda.Event(enable_timing=True)
@@ -516,6 +527,7 @@ def bench_autograd(dev, iters=20):
     out["two_d2d_copies_ms"] = round(2 * d2d, 4)
     for name in ("paper", "single_pass"):
         out[name]["frac_of_2x_d2d"] = round(2 * d2d / out[name]["fwd_bwd_ms"], 4)
+        out[name]["graph_frac_of_2x_d2d"] = round(2 * d2d / out[name]["graph_fwd_bwd_ms"], 4)
     return out
 
 

@@ -63,6 +63,10 @@ __global__ void __launch_bounds__(kThreads, 5)
     const uint32_t begin = blockIdx.x * per;
     if (begin >= total) return;
     const uint32_t end = total - begin > per ? begin + per : total;
+    // Launched with programmatic stream serialization (phase 2 is scheduled
+    // while phase 1 drains); nothing above touched global memory.
+    dev::grid_dependency_wait();
+    dev::allow_dependent_launch();
     uint32_t held0 = 0xffffffffu, held1 = 0xffffffffu;  // table held by each slot
 
     // Advance *a to the last entry whose first item is <= item, by doubling
@@ -164,10 +168,18 @@ template <int E_LOG>
 cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
 {
     const BatchEntry *ent = reinterpret_cast<const BatchEntry *>(dmem + g.entry_offset);
-    bmmc_batch_pass<E_LOG><<<g.grid, kThreads, g.smem, s>>>(ent, g.count,
-                                                           (uint32_t)g.total, dmem,
-                                                           g.tile_bytes);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = g.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bmmc_batch_pass<E_LOG>, ent, g.count, (uint32_t)g.total,
+                              static_cast<const uint8_t *>(dmem), g.tile_bytes);
 }
 
 template <int E_LOG>

@@ -94,3 +94,38 @@ def test_gradcheck_small():
     plan = bm.Plan(n, rows, c, 8)
     x = torch.randn(4, 1 << n, dtype=torch.float64, device="cuda", requires_grad=True)
     assert torch.autograd.gradcheck(lambda t: bmmc_permute(t, plan), (x,))
+
+
+@pytest.mark.parametrize("flags", [bm.BMMC_PLAN_PAPER, bm.BMMC_PLAN_SINGLE_PASS])
+def test_forward_backward_graph_capture(flags):
+    """Forward and backward captured in one CUDA graph: every replay gives
+    the eager result for the inputs written into the static buffers."""
+    import torch
+    n, rows_b = 12, 8
+    rows, c = wl.dense_bmmc(n, 21, _inv)
+    plan = bm.Plan(n, rows, c, 4, flags=flags)
+    x = torch.randn(rows_b, 1 << n, device="cuda", requires_grad=True)
+    w = torch.randn(rows_b, 1 << n, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):  # plans, inverse plans and allocator state
+            x.grad = None
+            bmmc_permute(x, plan).backward(w)
+    torch.cuda.current_stream().wait_stream(s)
+    x.grad = None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        y = bmmc_permute(x, plan)
+        y.backward(w)
+    dest = torch.from_numpy(_dest_index(n, rows, c)).cuda()
+    for seed in range(3):
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        with torch.no_grad():
+            x.copy_(torch.randn(x.shape, device="cuda", generator=gen))
+            w.copy_(torch.randn(w.shape, device="cuda", generator=gen))
+        g.replay()
+        torch.cuda.synchronize()
+        y_ref = torch.empty_like(w).scatter_(1, dest.expand(rows_b, -1), x.detach())
+        assert torch.equal(y, y_ref)
+        assert torch.equal(x.grad, w[:, dest])
