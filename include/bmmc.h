@@ -180,6 +180,28 @@ int bmmc_execute_ws(bmmc_plan p, const void *in, void *out, void *ws,
                     bmmc_stream_t stream);
 
 /*
+ * End to end with host buffers: copy host_in to dev_in, run the permutation
+ * dev_in -> dev_out, copy dev_out to host_out, in this order on `stream`
+ * (Sec. 3's out[A x + c] = in[x] with both arrays in host memory).  No
+ * counterpart in the paper, which times device-resident arrays only.
+ *
+ * host_in, host_out  host buffers of 2^n * elem_bytes bytes; pinned memory
+ *                    (cudaHostAlloc, cudaHostRegister) makes the copies
+ *                    asynchronous and lets them overlap kernels of other
+ *                    streams.  host_out holds the result once `stream` has
+ *                    reached the end of this call's work.
+ * dev_in, dev_out    caller-owned device staging buffers (conventions above).
+ * ws                 as for bmmc_execute_ws; NULL selects the plan-owned
+ *                    workspace of bmmc_execute for a two-pass plan.
+ * Calls on different streams with different staging buffers overlap: the
+ * upload of one call runs beside the kernels of another and the download
+ * of a third.
+ * Errors: INVALID, ALIAS, ALIGN, OOM, CUDA.
+ */
+int bmmc_execute_host(bmmc_plan p, const void *host_in, void *host_out, void *dev_in,
+                      void *dev_out, void *ws, bmmc_stream_t stream);
+
+/*
  * Run a plan without allocating any device memory.  The paper has no
  * counterpart; this entry point exists for callers that may not allocate:
  * code embedded in a host application that owns all device memory through

@@ -31,7 +31,7 @@ EXPORTED = (
     "bmmc_plan_create", "bmmc_plan_create_ex", "bmmc_plan_destroy",
     "bmmc_plan_num_passes", "bmmc_plan_matrix", "bmmc_plan_pass_matrix",
     "bmmc_plan_inverse",
-    "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws",
+    "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws", "bmmc_execute_host",
     "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
     "bmmc_strerror", "bmmc_plan_compose", "bmmc_parm_matrix", "bmmc_execute_ce",
     # include/bmmc_batch.h
@@ -108,6 +108,7 @@ def lib():
         "bmmc_plan_workspace_bytes": (ctypes.c_size_t, [vp]),
         "bmmc_execute": (ctypes.c_int, [vp, vp, vp, vp]),
         "bmmc_execute_ws": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bmmc_execute_host": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp]),
         "bmmc_execute_static_ws": (ctypes.c_int, [vp, vp, vp, vp]),
         "bmmc_plan_verify": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "bmmc_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -214,6 +215,11 @@ def bmmc_execute(h, in_ptr, out_ptr, stream=0):
 def bmmc_execute_ws(h, in_ptr, out_ptr, ws_ptr, stream=0):
     _check(lib().bmmc_execute_ws(h, in_ptr, out_ptr, ws_ptr, stream),
            "bmmc_execute_ws")
+
+
+def bmmc_execute_host(h, host_in, host_out, dev_in, dev_out, ws_ptr=None, stream=0):
+    _check(lib().bmmc_execute_host(h, host_in, host_out, dev_in, dev_out, ws_ptr, stream),
+           "bmmc_execute_host")
 
 
 def bmmc_execute_static_ws(h, in_ptr, out_ptr, stream=0):

@@ -262,6 +262,27 @@ int bmmc_execute_ws(bmmc_plan p, const void *in, void *out, void *ws, bmmc_strea
     return execute_impl(p, in, out, ws, (cudaStream_t)stream);
 }
 
+int bmmc_execute_host(bmmc_plan p, const void *host_in, void *host_out, void *dev_in,
+                      void *dev_out, void *ws, bmmc_stream_t stream)
+{
+    if (!p || !host_in || !host_out || !dev_in || !dev_out) return BMMC_ERR_INVALID;
+    const uint64_t bytes = array_bytes(p);
+    if (((uintptr_t)dev_in | (uintptr_t)dev_out) & 15u) return BMMC_ERR_ALIGN;
+    if (overlap(dev_in, dev_out, bytes) || overlap(host_in, host_out, bytes))
+        return BMMC_ERR_ALIAS;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(dev_in, host_in, (size_t)bytes, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return BMMC_ERR_CUDA;
+    const int rc = ws ? execute_impl(p, dev_in, dev_out, ws, s)
+                      : bmmc_execute(p, dev_in, dev_out, stream);
+    if (rc != BMMC_OK) return rc;
+    if (cudaMemcpyAsync(host_out, dev_out, (size_t)bytes, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return BMMC_ERR_CUDA;
+    return BMMC_OK;
+}
+
 int bmmc_execute_ce(bmmc_plan p, const void *in, void *out, void *ws, int key_type,
                     bmmc_stream_t stream)
 {

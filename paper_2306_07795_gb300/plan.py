@@ -107,6 +107,33 @@ class Plan:
             raise B.BmmcError(code, "bmmc_execute_ws")
         return out
 
+    def execute_host(self, host_in, host_out, dev_in, dev_out, stream=None, workspace=None):
+        """Host tensor host_in -> host tensor host_out through the device
+        staging tensors dev_in, dev_out (bmmc_execute_host: upload, the
+        plan's passes, download, in order on `stream`).  Asynchronous: read
+        host_out after the stream synchronises.  Pinned host tensors make the
+        copies overlap the kernels of other streams."""
+        import torch
+
+        for t, name in ((host_in, "host_in"), (host_out, "host_out")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous host tensor" % name)
+            if t.numel() * t.element_size() != self.nbytes:
+                raise ValueError("%s holds %d bytes, the plan needs %d"
+                                 % (name, t.numel() * t.element_size(), self.nbytes))
+        self._check_tensor(dev_in, "dev_in")
+        self._check_tensor(dev_out, "dev_out")
+        if stream is None:
+            stream = torch.cuda.current_stream(dev_in.device)
+        ws_ptr = workspace.data_ptr() if workspace is not None else None
+        with torch.cuda.device(dev_in.device):
+            code = B.lib().bmmc_execute_host(self._h, host_in.data_ptr(), host_out.data_ptr(),
+                                             dev_in.data_ptr(), dev_out.data_ptr(), ws_ptr,
+                                             stream.cuda_stream)
+        if code != B.BMMC_OK:
+            raise B.BmmcError(code, "bmmc_execute_host")
+        return host_out
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None:

@@ -168,6 +168,60 @@ def test_plan_owned_workspace_entry_point():
     assert torch.equal(out, p(x))
 
 
+@pytest.mark.parametrize("e", [4, 8, 16])
+def test_execute_host_buffers(e):
+    """bmmc_execute_host: pinned and pageable host buffers, caller and
+    plan-owned workspaces, three streams in flight; every result equals the
+    oracle's."""
+    import torch
+    n = 17
+    arr = wl.payload(n, e, seed=6)
+    flat = np.ascontiguousarray(arr).reshape(-1).view(np.uint8)
+    cases = [("bit_reverse", wl.bit_reverse(n), 0)] + \
+        [("dense_%d" % i,) + wl.dense_bmmc(n, 60 + i, oracle_invertible) for i in range(5)]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    jobs = []
+    for i, (name, rows, c) in enumerate(cases):
+        p = bm.Plan(n, rows, c, e)
+        pinned = i % 2 == 0
+        h_in = torch.from_numpy(flat.copy())
+        h_out = torch.zeros_like(h_in)
+        if pinned:
+            h_in, h_out = h_in.pin_memory(), h_out.pin_memory()
+        d_in = torch.empty(flat.size, dtype=torch.uint8, device="cuda")
+        d_out = torch.empty_like(d_in)
+        ws = None
+        if p.workspace_bytes and i % 3 == 1:
+            ws = torch.empty(p.workspace_bytes, dtype=torch.uint8, device="cuda")
+        p.execute_host(h_in, h_out, d_in, d_out, stream=streams[i % 3], workspace=ws)
+        jobs.append((name, p, rows, c, h_out, (h_in, d_in, d_out, ws)))
+    torch.cuda.synchronize()
+    for name, p, rows, c, h_out, _ in jobs:
+        want = np.ascontiguousarray(oracle.apply(n, rows, c, arr, elem_bytes=e))
+        assert np.array_equal(h_out.numpy(), want.reshape(-1).view(np.uint8)), name
+
+
+def test_execute_host_errors():
+    import torch
+    n = 12
+    p = bm.Plan(n, wl.bit_reverse(n), 0, 4)
+    h = torch.zeros(1 << n, dtype=torch.int32).pin_memory()
+    h2 = torch.zeros_like(h).pin_memory()
+    d = torch.zeros(1 << n, dtype=torch.int32, device="cuda")
+    d2 = torch.zeros_like(d)
+    lib = bm._binding.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.bmmc_execute_host(p.handle, h.data_ptr(), h2.data_ptr(), d.data_ptr() + 4,
+                                 d2.data_ptr(), None, s) == bm.BMMC_ERR_ALIGN
+    assert lib.bmmc_execute_host(p.handle, h.data_ptr(), h.data_ptr(), d.data_ptr(),
+                                 d2.data_ptr(), None, s) == bm.BMMC_ERR_ALIAS
+    assert lib.bmmc_execute_host(p.handle, h.data_ptr(), h2.data_ptr(), d.data_ptr(),
+                                 d.data_ptr(), None, s) == bm.BMMC_ERR_ALIAS
+    assert lib.bmmc_execute_host(p.handle, None, h2.data_ptr(), d.data_ptr(),
+                                 d2.data_ptr(), None, s) == bm.BMMC_ERR_INVALID
+    torch.cuda.synchronize()
+
+
 def test_concurrent_streams_distinct_workspaces():
     import torch
     n = 20
