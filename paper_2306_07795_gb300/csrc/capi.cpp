@@ -33,6 +33,9 @@ int elem_log(size_t e)
 
 uint64_t array_bytes(const bmmc_plan_s *p) { return (1ull << p->n) << p->e_log; }
 
+// Arrays up to this size take one pass whatever the matrix.
+constexpr uint64_t kWholeArrayBytes = 64 * 1024;
+
 bool overlap(const void *a, const void *b, uint64_t bytes)
 {
     uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
@@ -82,13 +85,15 @@ int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
     p->a = a;
     p->opt = opt;
 
-    // Classification (Sec. 5.1 / 5.2).  Arrays under 1 KiB and single-pass
-    // plans take one pass; otherwise a tiled matrix takes one pass and any
+    // Classification (Sec. 5.1 / 5.2).  Single-pass plans and arrays that
+    // fit one thread block's shared memory (at most kWholeArrayBytes; two
+    // launches would cost more than moving the array) take one pass over
+    // the generic tiles; otherwise a tiled matrix takes one pass and any
     // other is factorised into two tiled passes.
     int k = opt.seg_bits ? opt.seg_bits : default_seg_bits(e_log);
     if (k > n) k = n;
-    const bool tiny = ((1ull << (n + e_log)) < 1024);
-    if (tiny || opt.flags == BMMC_PLAN_SINGLE_PASS || f2::tiled_columns(a, k)) {
+    const bool small = ((1ull << (n + e_log)) <= kWholeArrayBytes);
+    if (small || opt.flags == BMMC_PLAN_SINGLE_PASS || f2::tiled_columns(a, k)) {
         p->npass = 1;
         p->t[0] = a;
         p->tc[0] = c;

@@ -258,14 +258,17 @@ def test_error_codes_on_device_pointers():
     with pytest.raises(bm.BmmcError) as ei:
         bm.bmmc_execute(p.handle, x.data_ptr(), 0, stream)
     assert ei.value.code == bm.BMMC_ERR_INVALID
-    rows, c = wl.dense_bmmc(n, 3, oracle_invertible)
-    p2 = bm.Plan(n, rows, c, 4)
+    n2 = 18  # above the one-pass size limit
+    rows, c = wl.dense_bmmc(n2, 3, oracle_invertible)
+    p2 = bm.Plan(n2, rows, c, 4)
     assert p2.num_passes == 2
+    x2 = torch.zeros(1 << n2, dtype=torch.int32, device="cuda")
+    y2 = torch.zeros_like(x2)
     with pytest.raises(bm.BmmcError) as ei:   # two-pass plan needs a workspace
-        bm.bmmc_execute_ws(p2.handle, x.data_ptr(), y.data_ptr(), None, stream)
+        bm.bmmc_execute_ws(p2.handle, x2.data_ptr(), y2.data_ptr(), None, stream)
     assert ei.value.code == bm.BMMC_ERR_INVALID
     with pytest.raises(bm.BmmcError) as ei:   # workspace overlapping the input
-        bm.bmmc_execute_ws(p2.handle, x.data_ptr(), y.data_ptr(), x.data_ptr(),
+        bm.bmmc_execute_ws(p2.handle, x2.data_ptr(), y2.data_ptr(), x2.data_ptr(),
                            stream)
     assert ei.value.code == bm.BMMC_ERR_ALIAS
 

@@ -88,7 +88,7 @@ def _k_for(e, n):
 
 @pytest.mark.parametrize("e", [4, 8, 16])
 def test_classification_and_factors(e):
-    n = 14
+    n = 16  # above the one-pass size limit (64 KiB) at every element size
     k = _k_for(e, n)
     cases = [wl.bit_reverse(n), wl.half_swap(n), wl.random_bp(n, 3)]
     cases.append(wl.tiled_only_bmmc(n, k, 9, oracle_invertible)[0])
@@ -109,6 +109,21 @@ def test_classification_and_factors(e):
             assert f2.is_tiled(t1, n, k) and f2.is_tiled(t2, n, k)
         assert p.workspace_bytes == (0 if tiled else (1 << n) * e)
         assert p.verify() == 0
+
+
+@pytest.mark.parametrize("e", [4, 8, 16])
+def test_small_arrays_take_one_pass(e):
+    """Arrays of at most 64 KiB take one pass for any matrix in the default
+    strategy; the next size up factorises a dense matrix into two."""
+    limit = 16 - {4: 2, 8: 3, 16: 4}[e]  # 2^limit elements = 64 KiB
+    for n in range(max(1, limit - 4), limit + 2):
+        for s in range(3):
+            rows, c = wl.dense_bmmc(n, 70 + s, oracle_invertible)
+            p = bm.Plan(n, rows, c, e)
+            k = _k_for(e, n)
+            want = 1 if (n <= limit or f2.is_tiled(rows, n, k)) else 2
+            assert p.num_passes == want, (n, s)
+            assert p.verify() == 0
 
 
 def test_single_pass_strategy_is_one_pass():
