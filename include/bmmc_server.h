@@ -4,13 +4,16 @@
  * Requests (one permutation of one array each) are submitted from any host
  * thread and served on the current device.  Two modes:
  *
- *  BMMC_SERVER_CONTINUOUS  A scheduler thread plans each submitted request,
- *      admits it as soon as its device bytes fit in the HBM budget, and
- *      launches it on the least-loaded of S streams, so that requests that
- *      arrive while others run start at once and overlap with them on the
- *      device.  Small requests that are admitted together are grouped into one
- *      persistent batch launch (bmmc_batch.h).  A completion check retires
- *      requests as their events fire and returns their bytes to the budget.
+ *  BMMC_SERVER_CONTINUOUS  A scheduler thread admits each submitted request
+ *      (planned in the submitting thread) as soon as its device bytes fit in
+ *      the HBM budget, and launches it on the least-loaded of S streams, so
+ *      that requests that arrive while others run start at once and overlap
+ *      with them on the device.  Small requests that are admitted together
+ *      are grouped into one persistent batch launch (bmmc_batch.h).  A request
+ *      that finds nothing queued ahead of it and the scheduler idle is
+ *      admitted and launched in the submitting thread instead.  A completion
+ *      check retires requests as their events fire and returns their bytes to
+ *      the budget.
  *  BMMC_SERVER_PLAIN  The baseline: bmmc_server_submit plans and launches the
  *      request in the calling thread, on one stream, in submission order, with
  *      no admission control and no grouping.

@@ -6,13 +6,16 @@
 // while their input + output + workspace bytes fit the budget and their output
 // and workspace fit the arena, launches each on the least-loaded stream (small
 // ones admitted together share one batch launch), and retires launches as
-// their events complete.  PLAIN mode does planning, allocation and launch in
-// the submitting thread on one stream.
+// their events complete.  A request that finds nothing queued ahead of it and
+// the scheduler idle is admitted and launched in the submitting thread.  PLAIN
+// mode does planning, allocation and launch in the submitting thread on one
+// stream.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -129,6 +132,9 @@ struct bmmc_server_s {
     std::condition_variable cv;       // new submissions / stop
     std::condition_variable drained;  // outstanding reached 0
     std::deque<Req *> submitted;
+    // requests the worker has taken from `submitted` and not yet queued in
+    // `waiting` (set under mu, cleared under sched_mu)
+    std::atomic<size_t> in_transit{0};
     std::vector<bmmc_server_result> results;
     uint64_t outstanding = 0;
     bool stop = false;
@@ -144,7 +150,8 @@ struct bmmc_server_s {
 
     // counters
     uint64_t n_submitted = 0, n_completed = 0, n_single = 0, n_groups = 0,
-             n_grouped = 0, peak_bytes = 0, peak_inflight = 0, n_inflight = 0;
+             n_grouped = 0, peak_bytes = 0, peak_inflight = 0, n_inflight = 0,
+             n_inline = 0;
 
     double now_ms() const
     {
@@ -353,12 +360,37 @@ bool admit(bmmc_server_s *s)
     const bool group = s->cfg.group_min > 0 && (int)small.size() >= s->cfg.group_min;
     if (group && launch_group(s, small, least_loaded(s))) {
         for (Req *r : admitted)
-            if (r->array_bytes > s->cfg.group_max_bytes) launch_single(s, r, least_loaded(s));
+            if (r->array_bytes > s->cfg.group_max_bytes)
+                launch_single(s, r, least_loaded(s));
     } else {
         for (Req *r : admitted) launch_single(s, r, least_loaded(s));
     }
     note_peaks(s);
     return true;
+}
+
+// Admit and launch one request now if the budget and the arena allow
+// (sched_mu held, nothing waiting ahead of it).
+bool admit_one(bmmc_server_s *s, Req *r)
+{
+    const bool idle = s->used == 0;
+    if (!idle && s->used + r->bytes > s->cfg.budget_bytes) return false;
+    if (!allocate(s, r)) return false;
+    s->used += r->bytes;
+    launch_single(s, r, least_loaded(s));
+    note_peaks(s);
+    return true;
+}
+
+// Make the server's device current in the calling thread; returns the
+// device to restore (or -1).
+int enter_device(const bmmc_server_s *s)
+{
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return -1;
+    if (cur == s->device) return -1;
+    cudaSetDevice(s->device);
+    return cur;
 }
 
 void worker_main(bmmc_server_s *s)
@@ -384,9 +416,11 @@ void worker_main(bmmc_server_s *s)
                 }
             }
             fresh.swap(s->submitted);
+            s->in_transit.store(fresh.size());
         }
         std::lock_guard<std::mutex> lk2(s->sched_mu);
         for (Req *r : fresh) s->waiting.push_back(r);
+        s->in_transit.store(0);
         bool progress = retire(s);
         progress |= admit(s);
         if (!progress && s->n_inflight) std::this_thread::yield();
@@ -477,11 +511,44 @@ int bmmc_server_submit(bmmc_server s, uint64_t id, int n, const uint64_t *A_rows
         return rc;
     }
     if (s->cfg.mode == BMMC_SERVER_CONTINUOUS) {
+        auto enqueue = [s, r]() {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->submitted.push_back(r);
+            s->cv.notify_one();
+            return BMMC_OK;
+        };
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->outstanding += 1;
+            s->n_submitted += 1;
+            if (s->hold || s->stop || !s->submitted.empty()) {
+                s->submitted.push_back(r);
+                s->cv.notify_one();
+                return BMMC_OK;
+            }
+        }
+        // Inline dispatch: when nothing submitted earlier is still queued
+        // and the scheduler is not busy, admit and launch in this thread, as
+        // the plain loop would, instead of waking the scheduler.  Requests
+        // taken by the scheduler but not yet queued (in_transit) keep their
+        // place: this one then queues behind them.
+        std::unique_lock<std::mutex> lk2(s->sched_mu, std::try_to_lock);
+        if (!lk2.owns_lock() || s->in_transit.load() != 0) {
+            if (lk2.owns_lock()) lk2.unlock();
+            return enqueue();
+        }
+        bool launched = false;
+        if (s->waiting.empty()) {
+            const int prev = enter_device(s);
+            retire(s);
+            launched = admit_one(s, r);
+            if (prev >= 0) cudaSetDevice(prev);
+        }
+        if (!launched) s->waiting.push_back(r);
+        if (launched) s->n_inline += 1;
+        lk2.unlock();
         std::lock_guard<std::mutex> lk(s->mu);
-        s->submitted.push_back(r);
-        s->outstanding += 1;
-        s->n_submitted += 1;
-        s->cv.notify_one();
+        s->cv.notify_one();  // the scheduler retires the launch, or admits r
         return BMMC_OK;
     }
     // PLAIN: allocate (waiting for completions if the arena is full), launch.
@@ -560,10 +627,11 @@ int bmmc_server_stats(bmmc_server s, char *buf, size_t len)
 {
     if (!s) return BMMC_ERR_INVALID;
     char tmp[512];
-    uint64_t single, groups, grouped, peak_b, peak_i, sub, comp;
+    uint64_t single, inl, groups, grouped, peak_b, peak_i, sub, comp;
     {
         std::lock_guard<std::mutex> lk(s->sched_mu);
         single = s->n_single;
+        inl = s->n_inline;
         groups = s->n_groups;
         grouped = s->n_grouped;
         peak_b = s->peak_bytes;
@@ -577,11 +645,13 @@ int bmmc_server_stats(bmmc_server s, char *buf, size_t len)
     int k = snprintf(tmp, sizeof(tmp),
                      "{\"mode\": \"%s\", \"streams\": %d, \"submitted\": %llu, "
                      "\"completed\": %llu, \"single_launches\": %llu, "
+                     "\"inline_launches\": %llu, "
                      "\"group_launches\": %llu, \"grouped_requests\": %llu, "
                      "\"peak_bytes_in_flight\": %llu, \"peak_requests_in_flight\": %llu}",
                      s->cfg.mode == BMMC_SERVER_PLAIN ? "plain" : "continuous", s->nstreams,
                      (unsigned long long)sub, (unsigned long long)comp,
-                     (unsigned long long)single, (unsigned long long)groups,
+                     (unsigned long long)single, (unsigned long long)inl,
+                     (unsigned long long)groups,
                      (unsigned long long)grouped, (unsigned long long)peak_b,
                      (unsigned long long)peak_i);
     if (buf && len) {

@@ -126,6 +126,32 @@ def test_held_requests_are_grouped(flags):
     srv.close()
 
 
+def test_idle_server_launches_inline():
+    """A request that finds the server idle is launched in the submitting
+    thread; its result is the same as alone, and a burst behind it still
+    queues (and is grouped) as before."""
+    import torch
+    reqs = _requests(8, rate=1e6, n_lo=12, n_hi=16, seed=31)
+    srv = serving.Server("cuda", budget_bytes=1 << 30, arena_bytes=1 << 30,
+                         group_max_bytes=1 << 22, group_min=2, keep_outputs=True)
+    by_id = {}
+    for r in reqs:  # one at a time: nothing is ever queued ahead
+        assert srv.submit(r.rid, r.n, r.rows, r.c, r.e, r.x) == bm.BMMC_OK
+        srv.drain()
+        for rid, st, _, _, out in srv.results():
+            by_id[rid] = (st, out)
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs)
+    assert stats["inline_launches"] >= 1, stats
+    assert stats["inline_launches"] <= stats["single_launches"]
+    for r in reqs:
+        st, r.out_ptr = by_id[r.rid]
+        assert st == bm.BMMC_OK
+        assert torch.equal(_output(r), _solo(r, bm.BMMC_PLAN_PAPER))
+        srv.release(r.out_ptr)
+    srv.close()
+
+
 def test_submit_errors():
     import torch
     srv = serving.Server("cuda", budget_bytes=1 << 30, arena_bytes=64 << 20)
