@@ -53,7 +53,8 @@ size_t bmmc_batch_table_bytes(const bmmc_plan *plans, int count);
  * batches never synchronises the device.  The buffers stay bound to the batch
  * until bmmc_batch_destroy.  Created for the current device.
  * Errors: INVALID, ALIGN, ALIAS, TOO_LARGE (a phase of 2^32 or more tiles),
- * OOM (host), CUDA.
+ * UNSUPPORTED (a plan whose tiles are too large to double-buffer in shared
+ * memory: cta_tile_log2 = 17), OOM (host), CUDA.
  */
 int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
                       const void *const *ins, void *const *outs, void *ws,

@@ -43,14 +43,19 @@ static_assert(sizeof(BatchEntry) == 32, "BatchEntry layout");
 constexpr uint32_t kDescSlot = (uint32_t)((sizeof(PassDesc) + 127) & ~(size_t)127);
 constexpr uint32_t kThreads = 256;
 
-// Shared memory: [table slot 0][table slot 1][tile buffer 0][tile buffer 1].
-// A block's items alternate between the slots: while one item is gathered and
-// stored from its buffer, the loads of the block's next item are already in
-// flight into the other buffer (cp.async groups).
+// Shared memory: `slots` table slots, then `slots` tile buffers (slots = 3,
+// or 2 when three tile buffers do not fit).  A block's items rotate over the
+// slots: while one item is gathered and stored from its buffer, the loads of
+// the block's next item are already in flight into the next buffer (cp.async
+// groups).  With three slots the loads issued for item i + 2 go to the buffer
+// item i - 1 used, which every thread finished reading before the barrier of
+// item i, so one barrier per item suffices; two slots need a second barrier
+// after the stores.  The last 16 bytes record which table each slot holds.
+constexpr uint32_t kMaxSlots = 3;
 template <int E_LOG>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 4)
     bmmc_batch_pass(const BatchEntry *__restrict__ ent, uint32_t count, uint32_t total,
-                    const uint8_t *__restrict__ descs, uint32_t tile_bytes)
+                    const uint8_t *__restrict__ descs, uint32_t tile_bytes, uint32_t slots)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
@@ -67,7 +72,12 @@ __global__ void __launch_bounds__(kThreads, 5)
     // while phase 1 drains); nothing above touched global memory.
     dev::grid_dependency_wait();
     dev::allow_dependent_launch();
-    uint32_t held0 = 0xffffffffu, held1 = 0xffffffffu;  // table held by each slot
+    // Table held by each slot, in shared memory after the tile buffers.
+    // Every thread writes the same value; it is read only after a barrier.
+    volatile uint32_t *held =
+        reinterpret_cast<volatile uint32_t *>(smem + slots * (kDescSlot + tile_bytes));
+    if (tid < kMaxSlots) held[tid] = 0xffffffffu;
+    __syncthreads();
 
     // Advance *a to the last entry whose first item is <= item, by doubling
     // steps and then bisection: O(log skipped) dependent loads, one for the
@@ -95,19 +105,20 @@ __global__ void __launch_bounds__(kThreads, 5)
     auto stage = [&](uint32_t item, int slot, uint32_t *a) {
         find(item, a);
         const uint32_t desc = ent[*a].desc;
-        if (desc != (slot ? held1 : held0)) {
+        if (desc != held[slot]) {
             const uint4 *src = reinterpret_cast<const uint4 *>(descs + (size_t)desc * kDescSlot);
             uint4 *dst = reinterpret_cast<uint4 *>(smem + slot * kDescSlot);
             for (uint32_t w = tid; w < kDescSlot / 16; w += blockDim.x) dst[w] = src[w];
             __syncthreads();
-            if (slot) held1 = desc;
-            else held0 = desc;
+            held[slot] = desc;
         }
     };
     auto table = [&](int slot) -> const PassDesc & {
         return *reinterpret_cast<const PassDesc *>(smem + slot * kDescSlot);
     };
-    auto buffer = [&](int slot) { return s0 + 2 * kDescSlot + (uint32_t)slot * tile_bytes; };
+    auto buffer = [&](int slot) {
+        return s0 + slots * kDescSlot + (uint32_t)slot * tile_bytes;
+    };
     // Thread part of the addresses of the pass last seen (consecutive items
     // of a block almost always belong to the same pass).
     uint32_t tp_desc = 0xffffffffu;
@@ -130,11 +141,12 @@ __global__ void __launch_bounds__(kThreads, 5)
     stage(begin, 0, &a_cur);
     issue(begin, a_cur, 0);
     int slot = 0;
-    for (uint32_t item = begin; item < end; ++item, slot ^= 1) {
+    for (uint32_t item = begin; item < end; ++item) {
+        const int next = slot + 1 == (int)slots ? 0 : slot + 1;
         uint32_t a_next = a_cur;
         if (item + 1 < end) {
-            stage(item + 1, slot ^ 1, &a_next);
-            issue(item + 1, a_next, slot ^ 1);
+            stage(item + 1, next, &a_next);
+            issue(item + 1, a_next, next);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -147,8 +159,9 @@ __global__ void __launch_bounds__(kThreads, 5)
             dev::tile_store<E_LOG, dev::kKeyNone>(d, addr(d, a_cur, item), ent[a_cur].dst,
                                                   buffer(slot));
         }
-        __syncthreads();  // buffer and table `slot` are free for the item after next
+        if (slots == 2) __syncthreads();  // buffer `slot` is free for item + 2
         a_cur = a_next;
+        slot = next;
     }
 }
 
@@ -160,6 +173,7 @@ struct Group {
     size_t entry_offset = 0;  // byte offset of its entries in the device block
     uint32_t smem = 0;
     uint32_t tile_bytes = 0;  // largest tile buffer of the group's passes
+    uint32_t slots = 0;       // tile buffers (3, or 2 when 3 do not fit)
     uint32_t grid = 0;
     uint32_t arrays = 0;
 };
@@ -179,7 +193,27 @@ cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, bmmc_batch_pass<E_LOG>, ent, g.count, (uint32_t)g.total,
-                              static_cast<const uint8_t *>(dmem), g.tile_bytes);
+                              static_cast<const uint8_t *>(dmem), g.tile_bytes, g.slots);
+}
+
+// Shared memory of a group with `slots` tile buffers.
+uint32_t group_smem(uint32_t slots, uint32_t tile_bytes)
+{
+    return slots * (kDescSlot + tile_bytes) + 16;
+}
+
+// Three tile buffers if they fit in a block's shared memory, else two;
+// false if not even two fit (tiles of 128 KiB).
+bool choose_slots(Group *g, int max_smem)
+{
+    for (uint32_t slots = kMaxSlots; slots >= 2; --slots) {
+        if (group_smem(slots, g->tile_bytes) <= (uint32_t)max_smem) {
+            g->slots = slots;
+            g->smem = group_smem(slots, g->tile_bytes);
+            return true;
+        }
+    }
+    return false;
 }
 
 template <int E_LOG>
@@ -346,7 +380,8 @@ int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
             if (g.total > 0xffffffffull) return BMMC_ERR_TOO_LARGE;
             g.arrays = g.count;
             g.tile_bytes = (max_smem + 127u) & ~127u;
-            g.smem = 2 * kDescSlot + 2 * g.tile_bytes;
+            g.slots = kMaxSlots;
+            g.smem = group_smem(g.slots, g.tile_bytes);
             groups.push_back(g);
         }
     }
@@ -355,7 +390,12 @@ int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
     if (cudaGetDevice(&dev) != cudaSuccess) return BMMC_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return BMMC_ERR_CUDA;
+    int max_smem = 0;
+    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+        return BMMC_ERR_CUDA;
     for (Group &g : groups) {
+        if (!choose_slots(&g, max_smem)) return BMMC_ERR_UNSUPPORTED;
         cudaError_t err = cudaSuccess;
         switch (g.e_log) {
         case 2: err = prepare_group<2>(&g, sms); break;

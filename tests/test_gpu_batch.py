@@ -124,3 +124,21 @@ def test_overlapping_buffers_rejected():
     with pytest.raises(bm.BmmcError) as ei:
         Batch([p, p], [a, b_], [b_, c])  # an output over another input
     assert ei.value.code == bm.BMMC_ERR_ALIAS
+
+
+def test_tile_size_limits():
+    """64 KiB tiles run with three tile buffers per block; 128 KiB tiles do
+    not fit a block's shared memory twice and are rejected at creation."""
+    import torch
+    n, e = 18, 4
+    ns, es = [n, n - 2, n], [e, e, e]
+    plans, ins, outs, host = _build(ns, es, bm.BMMC_PLAN_PAPER, seed0=40)
+    big = [bm.Plan(p.n, p.rows, p.c, p.elem_bytes, cta_tile_log2=16) for p in plans]
+    b = Batch(big, ins, outs)
+    b()
+    torch.cuda.synchronize()
+    _check(outs, host)
+    huge = [bm.Plan(p.n, p.rows, p.c, p.elem_bytes, cta_tile_log2=17) for p in plans]
+    with pytest.raises(bm.BmmcError) as ei:
+        Batch(huge, ins, outs)
+    assert ei.value.code == bm.BMMC_ERR_UNSUPPORTED
