@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "pass_desc.h"
 #include "tile_body.cuh"
 
@@ -38,7 +40,10 @@ __global__ void bmmc_naive_pass(const __grid_constant__ PassDesc d,
 
 constexpr int kMaxDevices = 64;
 constexpr int kSmemLimit = 128 * 1024;
-bool g_attr_set[kMaxDevices][3][7];
+// Per device, element size and key: the kernel's shared-memory limit has
+// been raised.  Atomic because plans may be executed from several threads;
+// two threads raising it at once both set the same value.
+std::atomic<bool> g_attr_set[kMaxDevices][3][7];
 
 // Every launch allows programmatic dependent launch: the kernels wait on the
 // grid dependency before their first global memory access, so a pass may be
@@ -71,11 +76,12 @@ cudaError_t launch_typed(const PassDesc &d, const void *in, void *out, cudaStrea
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    if (dev >= 0 && dev < kMaxDevices && !g_attr_set[dev][E_LOG - 2][KEY]) {
+    if (dev >= 0 && dev < kMaxDevices &&
+        !g_attr_set[dev][E_LOG - 2][KEY].load(std::memory_order_acquire)) {
         err = cudaFuncSetAttribute(bmmc_tiled_pass<E_LOG, KEY>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
         if (err != cudaSuccess) return err;
-        g_attr_set[dev][E_LOG - 2][KEY] = true;
+        g_attr_set[dev][E_LOG - 2][KEY].store(true, std::memory_order_release);
     }
     return launch_pdl(bmmc_tiled_pass<E_LOG, KEY>, dim3(1u << d.n_cta),
                       dim3(1u << d.thread_bits), d.smem_bytes, s, d, src, dst);
