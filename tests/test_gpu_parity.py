@@ -334,3 +334,47 @@ def test_max_size_n32_sampled():
     sampled_check(n, wl.bit_reverse(n), 0, PAPER)
     rows, c = wl.dense_bmmc(n, 2, oracle_invertible)
     sampled_check(n, rows, c, SINGLE)
+
+
+def test_plans_from_many_host_threads():
+    """Plans created and executed from several host threads at once (each
+    with its own stream and buffers) give the single-threaded results."""
+    import threading
+    import torch
+    n = 16
+    cases = []
+    for t in range(4):
+        for e in (4, 8, 16):
+            rows, c = wl.dense_bmmc(n, 500 + 10 * t + e, oracle_invertible)
+            cases.append((t, e, rows, c))
+    want = {}
+    for t, e, rows, c in cases:
+        x = wl.payload_torch(n, e, seed=t, device="cuda")
+        want[(t, e)] = (x, bm.Plan(n, rows, c, e)(x))
+    torch.cuda.synchronize()
+    errors = []
+
+    def worker(t):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                for rep in range(10):
+                    for tt, e, rows, c in cases:
+                        if tt != t:
+                            continue
+                        flags = bm.BMMC_PLAN_SINGLE_PASS if rep % 2 else bm.BMMC_PLAN_PAPER
+                        p = bm.Plan(n, rows, c, e, flags=flags)
+                        x, y_ref = want[(t, e)]
+                        y = p(x)
+                        st.synchronize()
+                        if not torch.equal(y, y_ref):
+                            errors.append((t, e, rep))
+        except Exception as exc:  # surfaced below
+            errors.append(repr(exc))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
