@@ -916,15 +916,28 @@ def main():
 
     del bufs
     torch.cuda.empty_cache()
+
+    # The legs below report the other configurations beside the headline; a
+    # leg that raises is recorded as an error in its place, so that it cannot
+    # take the headline line down with it.
+    def leg(key, fn, *a, **kw):
+        try:
+            extras[key] = fn(*a, **kw)
+        except Exception as exc:  # reported in the JSON line
+            extras[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            print("bench leg %s failed: %r" % (key, exc), file=sys.stderr)
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+
     if not args.no_autograd:
-        extras["autograd"] = bench_autograd(dev)
+        leg("autograd", bench_autograd, dev)
     if not args.no_small:
-        extras["n20_config"] = bench_n20(dev)
-        extras["sorting_network"] = bench_sorting(dev)
+        leg("n20_config", bench_n20, dev)
+        leg("sorting_network", bench_sorting, dev)
     if not args.no_batched:
-        extras["batched"] = bench_batched(dev, stream, count=args.batched_count)
+        leg("batched", bench_batched, dev, stream, count=args.batched_count)
     if not args.no_serving:
-        extras["serving"] = bench_serving(dev, seconds=args.serving_seconds)
+        leg("serving", bench_serving, dev, seconds=args.serving_seconds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
