@@ -49,7 +49,11 @@ typedef struct bmmc_server_config {
     int group_min;            /* group only when at least this many are ready */
     int keep_outputs;         /* 1: outputs stay allocated until
                                  bmmc_server_release; 0: freed on completion */
-    int reserved[6];          /* must be zero */
+    int plan_cache;           /* plans kept for reuse by later requests for the
+                                 same (n, A, c, elem_bytes); 0 = plan every
+                                 request anew.  Entries in use are pinned; the
+                                 least recently used free one is evicted */
+    int reserved[5];          /* must be zero */
 } bmmc_server_config;
 
 /* One finished request. */

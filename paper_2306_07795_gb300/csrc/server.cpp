@@ -24,6 +24,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "bmmc.h"
@@ -95,6 +96,8 @@ struct Req {
     uint64_t id = 0;
     const void *in = nullptr;
     bmmc_plan plan = nullptr;
+    bool cached = false;     // plan belongs to the plan cache (pinned by this request)
+    std::string key;         // its cache key
     size_t array_bytes = 0;  // 2^n * e
     size_t ws_bytes = 0;
     uint64_t bytes = 0;      // in + out + ws, for the budget
@@ -148,6 +151,18 @@ struct bmmc_server_s {
     std::map<void *, size_t> kept;  // kept outputs and their sizes
     uint64_t used = 0;
 
+    // Plan cache (plans are immutable, so requests for the same permutation
+    // share one).  An entry used by a request in flight is pinned; when the
+    // cache is full the least recently used unpinned entry is evicted.
+    struct CachedPlan {
+        bmmc_plan plan = nullptr;
+        uint32_t refs = 0;
+        uint64_t last = 0;
+    };
+    std::mutex plan_mu;
+    std::unordered_map<std::string, CachedPlan> plans;
+    uint64_t plan_tick = 0, n_plan_hits = 0;
+
     // counters
     uint64_t n_submitted = 0, n_completed = 0, n_single = 0, n_groups = 0,
              n_grouped = 0, peak_bytes = 0, peak_inflight = 0, n_inflight = 0,
@@ -174,6 +189,20 @@ cudaEvent_t take_event(bmmc_server_s *s)
     return e;
 }
 
+// Give back a request's plan: unpin a cached one, destroy any other.
+void release_plan(bmmc_server_s *s, Req *r)
+{
+    if (!r->plan) return;
+    if (r->cached) {
+        std::lock_guard<std::mutex> lk(s->plan_mu);
+        auto it = s->plans.find(r->key);
+        if (it != s->plans.end() && it->second.refs > 0) it->second.refs -= 1;
+    } else {
+        bmmc_plan_destroy(r->plan);
+    }
+    r->plan = nullptr;
+}
+
 // Completion of one launch (sched_mu held).  Records results, frees bytes.
 void finish(bmmc_server_s *s, Launch &L)
 {
@@ -197,7 +226,7 @@ void finish(bmmc_server_s *s, Launch &L)
             s->kept[r->out] = r->array_bytes;
         }
         done.push_back(res);
-        bmmc_plan_destroy(r->plan);
+        release_plan(s, r);
         delete r;
     }
     if (L.batch) bmmc_batch_destroy(L.batch);
@@ -427,20 +456,77 @@ void worker_main(bmmc_server_s *s)
     }
 }
 
-// Plan a request (caller's thread).
+// Put a new plan in the cache (plan_mu held), evicting the least recently
+// used unpinned entry if the cache is full.  False if every entry is pinned.
+bool cache_insert(bmmc_server_s *s, const std::string &key, bmmc_plan plan)
+{
+    if (s->plans.size() >= (size_t)s->cfg.plan_cache) {
+        auto victim = s->plans.end();
+        for (auto it = s->plans.begin(); it != s->plans.end(); ++it)
+            if (it->second.refs == 0 &&
+                (victim == s->plans.end() || it->second.last < victim->second.last))
+                victim = it;
+        if (victim == s->plans.end()) return false;
+        bmmc_plan_destroy(victim->second.plan);
+        s->plans.erase(victim);
+    }
+    auto &ent = s->plans[key];
+    ent.plan = plan;
+    ent.refs = 1;
+    ent.last = ++s->plan_tick;
+    return true;
+}
+
+// Plan a request (caller's thread), through the plan cache if it has one.
 int prepare(bmmc_server_s *s, Req *r, int n, const uint64_t *rows, uint64_t c, size_t e)
 {
-    bmmc_plan_options o;
-    memset(&o, 0, sizeof(o));
-    o.flags = s->cfg.plan_flags;
-    int rc = bmmc_plan_create_ex(&r->plan, n, rows, c, e, &o);
-    if (rc != BMMC_OK) return rc;
+    const bool use_cache = s->cfg.plan_cache > 0 && n >= 1 && n <= 64;
+    if (use_cache) {
+        // key: n, e, c and the rows, as raw bytes (the flags are the server's)
+        r->key.resize(sizeof(int) + sizeof(size_t) + sizeof(uint64_t) * (1 + (size_t)n));
+        char *k = &r->key[0];
+        memcpy(k, &n, sizeof(int));
+        memcpy(k + sizeof(int), &e, sizeof(size_t));
+        memcpy(k + sizeof(int) + sizeof(size_t), &c, sizeof(uint64_t));
+        memcpy(k + sizeof(int) + sizeof(size_t) + sizeof(uint64_t), rows,
+               sizeof(uint64_t) * (size_t)n);
+        std::lock_guard<std::mutex> lk(s->plan_mu);
+        auto it = s->plans.find(r->key);
+        if (it != s->plans.end()) {
+            it->second.refs += 1;
+            it->second.last = ++s->plan_tick;
+            r->plan = it->second.plan;
+            r->cached = true;
+            s->n_plan_hits += 1;
+        }
+    }
+    if (!r->plan) {
+        bmmc_plan_options o;
+        memset(&o, 0, sizeof(o));
+        o.flags = s->cfg.plan_flags;
+        bmmc_plan p = nullptr;
+        int rc = bmmc_plan_create_ex(&p, n, rows, c, e, &o);
+        if (rc != BMMC_OK) return rc;
+        r->plan = p;
+        if (use_cache) {
+            std::lock_guard<std::mutex> lk(s->plan_mu);
+            auto it = s->plans.find(r->key);
+            if (it != s->plans.end()) {  // planned meanwhile by another thread
+                bmmc_plan_destroy(p);
+                it->second.refs += 1;
+                it->second.last = ++s->plan_tick;
+                r->plan = it->second.plan;
+                r->cached = true;
+            } else {
+                r->cached = cache_insert(s, r->key, p);
+            }
+        }
+    }
     r->array_bytes = ((size_t)1 << n) * e;
     r->ws_bytes = bmmc_plan_workspace_bytes(r->plan);
     r->bytes = 2 * (uint64_t)r->array_bytes + r->ws_bytes;
     if (align_up(r->array_bytes) + align_up(r->ws_bytes) > s->arena.size()) {
-        bmmc_plan_destroy(r->plan);
-        r->plan = nullptr;
+        release_plan(s, r);
         return BMMC_ERR_TOO_LARGE;
     }
     return BMMC_OK;
@@ -461,6 +547,7 @@ int bmmc_server_create(bmmc_server *out, const bmmc_server_config *cfg)
     if (cfg->streams < 1 || cfg->streams > kMaxStreams) return BMMC_ERR_UNSUPPORTED;
     if (cfg->arena_bytes < kAlign || cfg->budget_bytes == 0) return BMMC_ERR_UNSUPPORTED;
     if (cfg->plan_flags > BMMC_PLAN_SINGLE_PASS) return BMMC_ERR_UNSUPPORTED;
+    if (cfg->plan_cache < 0) return BMMC_ERR_UNSUPPORTED;
     bmmc_server_s *s = new (std::nothrow) bmmc_server_s();
     if (!s) return BMMC_ERR_OOM;
     s->cfg = *cfg;
@@ -561,7 +648,7 @@ int bmmc_server_submit(bmmc_server s, uint64_t id, int n, const uint64_t *A_rows
     retire(s);
     while (!allocate(s, r)) {
         if (s->inflight[0].empty()) {  // cannot happen: prepare checked the size
-            bmmc_plan_destroy(r->plan);
+            release_plan(s, r);
             delete r;
             return BMMC_ERR_OOM;
         }
@@ -626,8 +713,8 @@ int bmmc_server_release(bmmc_server s, void *out)
 int bmmc_server_stats(bmmc_server s, char *buf, size_t len)
 {
     if (!s) return BMMC_ERR_INVALID;
-    char tmp[512];
-    uint64_t single, inl, groups, grouped, peak_b, peak_i, sub, comp;
+    char tmp[768];
+    uint64_t single, inl, groups, grouped, peak_b, peak_i, sub, comp, hits, cached;
     {
         std::lock_guard<std::mutex> lk(s->sched_mu);
         single = s->n_single;
@@ -642,18 +729,25 @@ int bmmc_server_stats(bmmc_server s, char *buf, size_t len)
         sub = s->n_submitted;
         comp = s->n_completed;
     }
+    {
+        std::lock_guard<std::mutex> lk(s->plan_mu);
+        hits = s->n_plan_hits;
+        cached = s->plans.size();
+    }
     int k = snprintf(tmp, sizeof(tmp),
                      "{\"mode\": \"%s\", \"streams\": %d, \"submitted\": %llu, "
                      "\"completed\": %llu, \"single_launches\": %llu, "
                      "\"inline_launches\": %llu, "
                      "\"group_launches\": %llu, \"grouped_requests\": %llu, "
-                     "\"peak_bytes_in_flight\": %llu, \"peak_requests_in_flight\": %llu}",
+                     "\"peak_bytes_in_flight\": %llu, \"peak_requests_in_flight\": %llu, "
+                     "\"plan_cache_hits\": %llu, \"plans_cached\": %llu}",
                      s->cfg.mode == BMMC_SERVER_PLAIN ? "plain" : "continuous", s->nstreams,
                      (unsigned long long)sub, (unsigned long long)comp,
                      (unsigned long long)single, (unsigned long long)inl,
                      (unsigned long long)groups,
                      (unsigned long long)grouped, (unsigned long long)peak_b,
-                     (unsigned long long)peak_i);
+                     (unsigned long long)peak_i, (unsigned long long)hits,
+                     (unsigned long long)cached);
     if (buf && len) {
         size_t cpy = (size_t)k < len - 1 ? (size_t)k : len - 1;
         memcpy(buf, tmp, cpy);
@@ -686,6 +780,7 @@ void bmmc_server_destroy(bmmc_server s)
     if (s->start) cudaEventDestroy(s->start);
     if (s->arena_mem) cudaFree(s->arena_mem);
     if (prev >= 0) cudaSetDevice(prev);
+    for (auto &kv : s->plans) bmmc_plan_destroy(kv.second.plan);
     delete s;
 }
 

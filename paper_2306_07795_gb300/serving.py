@@ -48,7 +48,7 @@ class Request:
 class Server:
     def __init__(self, device, mode="continuous", streams=4, budget_bytes=40 * 10**9,
                  arena_bytes=None, flags=B.BMMC_PLAN_PAPER, group_max_bytes=1 << 22,
-                 group_min=4, keep_outputs=False):
+                 group_min=4, keep_outputs=False, plan_cache=None):
         import torch
         self.device = torch.device(device)
         cfg = B.bmmc_server_config()
@@ -60,6 +60,10 @@ class Server:
         cfg.group_max_bytes = int(group_max_bytes)
         cfg.group_min = group_min
         cfg.keep_outputs = 1 if keep_outputs else 0
+        # the plain baseline plans every request; the server keeps plans
+        if plan_cache is None:
+            plan_cache = 0 if mode == "plain" else 1024
+        cfg.plan_cache = int(plan_cache)
         self.mode = mode
         with torch.cuda.device(self.device):
             self._h = B.bmmc_server_create(cfg)

@@ -152,6 +152,67 @@ def test_idle_server_launches_inline():
     srv.close()
 
 
+def _repeated(count, distinct, n=14, e=4, seed=41):
+    """count requests cycling over `distinct` dense permutations."""
+    mats = [wl.dense_bmmc(n, seed + j, _inv) for j in range(distinct)]
+    reqs = []
+    for i in range(count):
+        rows, c = mats[i % distinct]
+        x = wl.payload_torch(n, e, seed=i, device="cuda")
+        reqs.append(serving.Request(i, 0.0, n, e, rows, c, x))
+    return reqs
+
+
+@pytest.mark.parametrize("mode", ["continuous", "plain"])
+def test_plan_cache_reuses_plans(mode):
+    """Requests for the same permutation share one cached plan; every result
+    is still the same as alone."""
+    import torch
+    reqs = _repeated(24, 3)
+    srv = serving.Server("cuda", mode=mode, budget_bytes=1 << 30, arena_bytes=1 << 30,
+                         keep_outputs=True, plan_cache=8)
+    serving.drive(srv, reqs)
+    st = srv.stats()
+    assert st["completed"] == len(reqs)
+    assert st["plans_cached"] == 3
+    assert st["plan_cache_hits"] >= len(reqs) - 3 * 2  # at most a race per plan
+    for r in reqs:
+        assert r.status == bm.BMMC_OK
+        assert torch.equal(_output(r), _solo(r, bm.BMMC_PLAN_PAPER))
+        srv.release(r.out_ptr)
+    srv.close()
+
+
+def test_plan_cache_eviction_and_pinning():
+    """A cache of two plans: entries in use by held requests stay pinned (the
+    others are planned uncached), and later ones evict the least recently
+    used free entry."""
+    import torch
+    reqs = _repeated(6, 6, seed=61)
+    srv = serving.Server("cuda", budget_bytes=1 << 30, arena_bytes=1 << 30,
+                         keep_outputs=True, plan_cache=2)
+    srv.hold(True)  # all six are planned while none has finished
+    for r in reqs:
+        assert srv.submit(r.rid, r.n, r.rows, r.c, r.e, r.x) == bm.BMMC_OK
+    srv.hold(False)
+    srv.drain()
+    assert srv.stats()["plans_cached"] == 2
+    more = _repeated(4, 4, seed=71)
+    for r in more:  # one at a time: each finds a free entry to evict
+        r.rid += 100
+        assert srv.submit(r.rid, r.n, r.rows, r.c, r.e, r.x) == bm.BMMC_OK
+        srv.drain()
+    st = srv.stats()
+    assert st["plans_cached"] == 2 and st["plan_cache_hits"] == 0
+    by_id = {rid: (status, out) for rid, status, _, _, out in srv.results()}
+    for r in reqs + more:
+        status, r.out_ptr = by_id[r.rid]
+        assert status == bm.BMMC_OK
+        assert torch.equal(_output(r), _solo(r, bm.BMMC_PLAN_PAPER))
+        srv.release(r.out_ptr)
+    srv.close()
+
+
 def test_submit_errors():
     import torch
     srv = serving.Server("cuda", budget_bytes=1 << 30, arena_bytes=64 << 20)
