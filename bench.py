@@ -625,12 +625,22 @@ def bench_serving(dev, seconds=10.0, rate=2000.0, seed=11, budget=40 * 10**9, st
     pool = torch.randint(-2**31, 2**31 - 1, ((1 << 27) * 8 // 4,), dtype=torch.int32,
                          device=dev, generator=gen)
 
-    def requests(speedup=1.0, limit_s=None):
+    # For the repeated-matrix extra: 4 matrices per (n, kind), reused.
+    reuse = {}
+    for s, m in zip(specs, mats):
+        lst = reuse.setdefault((s["n"], s["kind"]), [])
+        if len(lst) < 4:
+            lst.append(m)
+
+    def requests(speedup=1.0, limit_s=None, repeated=False):
         out = []
         for i, (s, (rows, c)) in enumerate(zip(specs, mats)):
             t = s["arrival"] / speedup
             if limit_s is not None and t >= limit_s:
                 break
+            if repeated:
+                lst = reuse[(s["n"], s["kind"])]
+                rows, c = lst[i % len(lst)]
             x = pool[: (1 << s["n"]) * s["e"] // 4]
             out.append(serving.Request(i, t, s["n"], s["e"], rows, c, x))
         return out
@@ -641,12 +651,12 @@ def bench_serving(dev, seconds=10.0, rate=2000.0, seed=11, budget=40 * 10**9, st
             d[f] = round(d[f], 4)
         return d
 
-    def compare(flags, speedup=1.0, limit_s=None):
+    def compare(flags, speedup=1.0, limit_s=None, repeated=False):
         out = {}
         for mode, key in (("continuous", "server"), ("plain", "plain")):
             srv = serving.Server(dev, mode=mode, streams=streams, budget_bytes=budget,
                                  flags=flags)
-            reqs = serving.drive(srv, requests(speedup, limit_s))
+            reqs = serving.drive(srv, requests(speedup, limit_s, repeated))
             out[key] = rounded(serving.summarize(reqs))
             out[key]["stats"] = srv.stats()
             srv.close()
@@ -670,6 +680,12 @@ def bench_serving(dev, seconds=10.0, rate=2000.0, seed=11, budget=40 * 10**9, st
         row = {"rate_per_s": rate * fast}
         row.update(compare(bm.BMMC_PLAN_PAPER, speedup=fast, limit_s=2.0))
         res["extra_rate_sweep"].append(row)
+    # Extra: the configured stream for 2 s, but with the matrices drawn from 4
+    # per (n, kind), so that the server's plan cache hits (the plain loop
+    # still plans every request).
+    res["extra_repeated_matrices"] = {"rate_per_s": rate, "matrices_per_size_and_kind": 4}
+    res["extra_repeated_matrices"].update(compare(bm.BMMC_PLAN_PAPER, limit_s=2.0,
+                                                  repeated=True))
     del pool
     torch.cuda.empty_cache()
     return res

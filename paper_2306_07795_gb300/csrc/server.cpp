@@ -19,6 +19,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -157,11 +158,12 @@ struct bmmc_server_s {
     struct CachedPlan {
         bmmc_plan plan = nullptr;
         uint32_t refs = 0;
-        uint64_t last = 0;
+        std::list<const std::string *>::iterator lru;  // valid while refs == 0
     };
     std::mutex plan_mu;
     std::unordered_map<std::string, CachedPlan> plans;
-    uint64_t plan_tick = 0, n_plan_hits = 0;
+    std::list<const std::string *> lru;  // unpinned entries, least recent first
+    uint64_t n_plan_hits = 0;
 
     // counters
     uint64_t n_submitted = 0, n_completed = 0, n_single = 0, n_groups = 0,
@@ -196,7 +198,8 @@ void release_plan(bmmc_server_s *s, Req *r)
     if (r->cached) {
         std::lock_guard<std::mutex> lk(s->plan_mu);
         auto it = s->plans.find(r->key);
-        if (it != s->plans.end() && it->second.refs > 0) it->second.refs -= 1;
+        if (it != s->plans.end() && it->second.refs > 0 && --it->second.refs == 0)
+            it->second.lru = s->lru.insert(s->lru.end(), &it->first);
     } else {
         bmmc_plan_destroy(r->plan);
     }
@@ -461,20 +464,24 @@ void worker_main(bmmc_server_s *s)
 bool cache_insert(bmmc_server_s *s, const std::string &key, bmmc_plan plan)
 {
     if (s->plans.size() >= (size_t)s->cfg.plan_cache) {
-        auto victim = s->plans.end();
-        for (auto it = s->plans.begin(); it != s->plans.end(); ++it)
-            if (it->second.refs == 0 &&
-                (victim == s->plans.end() || it->second.last < victim->second.last))
-                victim = it;
-        if (victim == s->plans.end()) return false;
-        bmmc_plan_destroy(victim->second.plan);
-        s->plans.erase(victim);
+        if (s->lru.empty()) return false;
+        const std::string victim = *s->lru.front();
+        s->lru.pop_front();
+        auto it = s->plans.find(victim);
+        bmmc_plan_destroy(it->second.plan);
+        s->plans.erase(it);
     }
     auto &ent = s->plans[key];
     ent.plan = plan;
     ent.refs = 1;
-    ent.last = ++s->plan_tick;
     return true;
+}
+
+// Pin a cached entry for one more request (plan_mu held).
+bmmc_plan cache_pin(bmmc_server_s *s, bmmc_server_s::CachedPlan &ent)
+{
+    if (ent.refs++ == 0) s->lru.erase(ent.lru);
+    return ent.plan;
 }
 
 // Plan a request (caller's thread), through the plan cache if it has one.
@@ -493,9 +500,7 @@ int prepare(bmmc_server_s *s, Req *r, int n, const uint64_t *rows, uint64_t c, s
         std::lock_guard<std::mutex> lk(s->plan_mu);
         auto it = s->plans.find(r->key);
         if (it != s->plans.end()) {
-            it->second.refs += 1;
-            it->second.last = ++s->plan_tick;
-            r->plan = it->second.plan;
+            r->plan = cache_pin(s, it->second);
             r->cached = true;
             s->n_plan_hits += 1;
         }
@@ -513,9 +518,7 @@ int prepare(bmmc_server_s *s, Req *r, int n, const uint64_t *rows, uint64_t c, s
             auto it = s->plans.find(r->key);
             if (it != s->plans.end()) {  // planned meanwhile by another thread
                 bmmc_plan_destroy(p);
-                it->second.refs += 1;
-                it->second.last = ++s->plan_tick;
-                r->plan = it->second.plan;
+                r->plan = cache_pin(s, it->second);
                 r->cached = true;
             } else {
                 r->cached = cache_insert(s, r->key, p);
