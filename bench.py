@@ -854,6 +854,24 @@ def main():
                                    "passes": 1, "count": len(sp_plans)}
         extras["single_pass_dense"] = sp
 
+    # The legs below report the other configurations beside the headline; a
+    # leg that raises is recorded as an error in its place, so that it cannot
+    # take the headline line down with it.
+    def leg(key, fn, *a, **kw):
+        try:
+            extras[key] = fn(*a, **kw)
+        except Exception as exc:  # reported in the JSON line
+            extras[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            print("bench leg %s failed: %r" % (key, exc), file=sys.stderr)
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+
+    # The L2-resident legs run before the end-to-end leg's large staging
+    # allocations (after those, the same replays measured 10-25 % slower).
+    if not args.no_small:
+        leg("n20_config", bench_n20, dev)
+        leg("sorting_network", bench_sorting, dev)
+
     # ---- end to end through the public API with host buffers --------------
     e2e = None
     if not args.no_e2e:
@@ -933,23 +951,8 @@ def main():
     del bufs
     torch.cuda.empty_cache()
 
-    # The legs below report the other configurations beside the headline; a
-    # leg that raises is recorded as an error in its place, so that it cannot
-    # take the headline line down with it.
-    def leg(key, fn, *a, **kw):
-        try:
-            extras[key] = fn(*a, **kw)
-        except Exception as exc:  # reported in the JSON line
-            extras[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
-            print("bench leg %s failed: %r" % (key, exc), file=sys.stderr)
-        torch.cuda.synchronize(dev)
-        torch.cuda.empty_cache()
-
     if not args.no_autograd:
         leg("autograd", bench_autograd, dev)
-    if not args.no_small:
-        leg("n20_config", bench_n20, dev)
-        leg("sorting_network", bench_sorting, dev)
     if not args.no_batched:
         leg("batched", bench_batched, dev, stream, count=args.batched_count)
     if not args.no_serving:
