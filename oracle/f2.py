@@ -164,6 +164,27 @@ def cyclic_shift_perm(n):
 # Whole-array application (Sec. 3 definition, scatter form as in Sec. 4.1)
 # ---------------------------------------------------------------------------
 
+def index_of(rows, c, xs):
+    """A x + c (Sec. 3) for every x of the uint64 array xs.
+
+    Bit i of the result is the parity of rows[i] & x (a popcount, where numpy
+    has one), XOR bit i of c.
+    """
+    xs = np.asarray(xs, dtype=np.uint64)
+    y = np.zeros_like(xs)
+    count = getattr(np, "bitwise_count", None)
+    for i, row in enumerate(rows):
+        masked = xs & np.uint64(row)
+        if count is not None:
+            par = (count(masked) & 1).astype(np.uint64)
+        else:
+            par = np.zeros_like(masked)
+            for b in range(64):
+                par ^= (masked >> np.uint64(b)) & np.uint64(1)
+        y |= par << np.uint64(i)
+    return y ^ np.uint64(c)
+
+
 def index_table(n, rows, c):
     """The destination A x + c of every x in [0, 2^n), as a uint64 array.
 

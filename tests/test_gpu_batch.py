@@ -142,3 +142,51 @@ def test_tile_size_limits():
     with pytest.raises(bm.BmmcError) as ei:
         Batch(huge, ins, outs)
     assert ei.value.code == bm.BMMC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("flags", [bm.BMMC_PLAN_PAPER, bm.BMMC_PLAN_SINGLE_PASS])
+def test_batched_config_full_size(flags):
+    """The batched configuration at full size, launched as the benchmark
+    launches it: 4096 int32 arrays with n uniform in 10..24 (seed 7), each
+    with its own dense random BMMC and c, one batch with the tile options the
+    autotuner picks there (512-byte segments, 64 KiB per block).  Each array
+    holds its own indices tagged with the array's number, so an element read
+    from the wrong array shows.  Arrays of at most 2^16 elements and 32
+    larger ones are checked element by element through the oracle's C loop;
+    every other array at 8192 random indices (and its first and last)."""
+    import torch
+    ns = wl.batched_sizes(count=4096, lo=10, hi=24, seed=7)
+    mats = [wl.dense_bmmc(n, 7 * 100003 + i, _inv) for i, n in enumerate(ns)]
+    sizes = [(1 << n) * 4 for n in ns]
+    offs, total = [], 0
+    for s in sizes:
+        offs.append(total)
+        total += (s + 255) // 256 * 256
+    xin = torch.empty(total // 4, dtype=torch.int32, device="cuda")
+    xout = torch.full_like(xin, -1)
+    ins = [xin[o // 4:(o + s) // 4] for o, s in zip(offs, sizes)]
+    outs = [xout[o // 4:(o + s) // 4] for o, s in zip(offs, sizes)]
+    for i, (n, x) in enumerate(zip(ns, ins)):
+        x.copy_(torch.arange(1 << n, dtype=torch.int32, device="cuda") | ((i & 0x7F) << 24))
+    plans = [bm.Plan(n, rows, c, 4, flags=flags, seg_bits=7, cta_tile_log2=16)
+             for n, (rows, c) in zip(ns, mats)]
+    b = Batch(plans, ins, outs)
+    b()
+    torch.cuda.synchronize()
+    del b
+    g = wl.rng(99)
+    large = [i for i, n in enumerate(ns) if n > 16]
+    whole = set(int(i) for i in g.choice(large, size=32, replace=False))
+    for i, (n, (rows, c), y) in enumerate(zip(ns, mats, outs)):
+        tag = (i & 0x7F) << 24
+        if n <= 16 or i in whole:
+            want_in = np.arange(1 << n, dtype=np.int32) | np.int32(tag)
+            bad = oracle.count_mismatch(n, rows, c, want_in, y.cpu().numpy(), elem_bytes=4)
+            assert bad == 0, (i, n, bad)
+        else:
+            xs = g.integers(0, 1 << n, size=8192, dtype=np.uint64)
+            xs[:2] = [0, (1 << n) - 1]
+            ys = f2.index_of(rows, c, xs)
+            got = y[torch.from_numpy(ys.astype(np.int64)).cuda()].cpu().numpy()
+            want = xs.astype(np.int64).astype(np.int32) | np.int32(tag)
+            assert np.array_equal(got, want), (i, n)

@@ -229,3 +229,42 @@ def test_submit_errors():
     res = srv.results()
     assert [r[0] for r in res] == [2] and res[0][1] == bm.BMMC_OK
     srv.close()
+
+
+def test_serving_config_full_size():
+    """The serving configuration's first 160 requests at full size (n uniform
+    in 12..27, 4- and 8-byte elements, 20 % BP and 80 % dense, seed 11), at
+    their Poisson arrival times, through the server as the benchmark runs it
+    (4 streams, 40 GB budget).  Every output is checked at 4096 random
+    indices (and the first and last) against the oracle's destinations."""
+    import torch
+    specs = wl.serving_requests(rate=2000.0, seconds=10.0, seed=11)[:160]
+    # one input pool: int32 iota, so every element's value names its index
+    pool = torch.arange(1 << 28, dtype=torch.int32, device="cuda")
+    reqs = []
+    for i, s in enumerate(specs):
+        n, e = s["n"], s["e"]
+        if s["kind"] == "bp":
+            rows, c = wl.random_bp(n, s["seed"]), 0
+        else:
+            rows, c = wl.dense_bmmc(n, s["seed"], _inv)
+        x = pool[: (1 << n) * e // 4]
+        reqs.append(serving.Request(i, s["arrival"], n, e, rows, c, x))
+    srv = serving.Server("cuda", streams=4, budget_bytes=40 * 10**9,
+                         arena_bytes=40 * 10**9, keep_outputs=True)
+    serving.drive(srv, reqs)
+    assert srv.stats()["completed"] == len(reqs)
+    g = wl.rng(5)
+    words = {4: 1, 8: 2}
+    for r in reqs:
+        assert r.status == bm.BMMC_OK, r.rid
+        w = words[r.e]
+        xs = g.integers(0, 1 << r.n, size=4096, dtype=np.uint64)
+        xs[:2] = [0, (1 << r.n) - 1]
+        ys = f2.index_of(r.rows, r.c, xs).astype(np.int64)
+        out = _output(r).view(torch.int32).view(-1, w)
+        got = out[torch.from_numpy(ys).cuda()].cpu().numpy()
+        want = (xs.astype(np.int64)[:, None] * w + np.arange(w)).astype(np.int32)
+        assert np.array_equal(got, want), (r.rid, r.n, r.e)
+        srv.release(r.out_ptr)
+    srv.close()

@@ -447,3 +447,16 @@ def test_merge_needs_sorted_halves():
     # ... but some arbitrary input is not (merge alone is not a sorter)
     assert any(f2.merge(3, [(v >> i) & 1 for i in range(8)])
                != sorted((v >> i) & 1 for i in range(8)) for v in range(256))
+
+
+@pytest.mark.parametrize("n", [1, 7, 24, 32])
+def test_index_of_matches_mat_vec(n):
+    """The vectorised destination formula agrees with the scalar definition
+    (pinned by the examples above) on random and extreme indices."""
+    g = wl.rng(300 + n)
+    rows, c = wl.dense_bmmc(n, 5, lambda r: f2.is_invertible(r, n))
+    xs = g.integers(0, 1 << n, size=500, dtype=np.uint64)
+    xs[:2] = [0, (1 << n) - 1]
+    got = f2.index_of(rows, c, xs)
+    want = [f2.bmmc_index(rows, c, int(x)) for x in xs]
+    assert got.tolist() == want
