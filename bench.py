@@ -347,8 +347,13 @@ def reference_arm(args):
         "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "n=28 BMMC permutation set (bounded 2^24 sample)",
-                   "n": n_sample, "elem_bytes": [4, 8, 16]},
+        "config": {"workload": "n=28 BMMC permutation set per elem size: bit-reversal, "
+                               "half-swap, %d random BP, %d random tiled-only, %d random "
+                               "dense (random c)" % (args.bp, args.tiled, args.dense),
+                   "n": args.n, "elem_bytes": [int(v) for v in args.elem.split(",")],
+                   "strategy": args.strategy,
+                   "reference_sample": "each step: one permutation of each class per "
+                                       "element size at 2^%d elements" % n_sample},
         "cpu_baseline": {"value": value, "unit": "GB/s",
                          "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": "2^24 elements, one permutation of each class "
