@@ -26,6 +26,10 @@
  *    legacy default stream.  Launch errors are returned synchronously as
  *    BMMC_ERR_CUDA; faults during execution surface at the caller's next
  *    synchronisation with the stream.
+ *  - Passes are launched with programmatic dependent launch: a pass may be
+ *    scheduled while the previous kernel of its stream drains, but it reads
+ *    or writes memory only after that kernel has completed, so stream order
+ *    holds as for any launch (and inside CUDA graphs).
  *  - All functions return BMMC_OK (0) or a negative BMMC_ERR_* code, except
  *    where stated otherwise.
  */
