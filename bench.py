@@ -295,14 +295,27 @@ def oracle_sample(n_sample=24, elems=(4, 8, 16)):
     return items
 
 
-def run_oracle_step(n_sample, items, buffers):
+def run_oracle_step(n_sample, items, buffers, threads=True):
     import oracle
     moved = 0
     for cls, e, rows, c in items:
         inp = buffers[e]
-        oracle.apply(n_sample, rows, c, inp, elem_bytes=e)
+        oracle.apply(n_sample, rows, c, inp, elem_bytes=e, threads=threads)
         moved += 2 * (1 << n_sample) * e
     return moved
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), or the platform's processor string."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline(n_sample=24, reps=1):
@@ -316,12 +329,34 @@ def cpu_baseline(n_sample=24, reps=1):
     for _ in range(reps):
         moved += run_oracle_step(n_sample, items, buffers)
     dt = time.perf_counter() - t0
-    return {"value": moved / dt / 1e9, "unit": "GB/s",
-            "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": ("C loop out[A x + c] = in[x] (OpenMP over x), 2^%d elements, "
-                       "one bit-reversal, half-swap, random BP, tiled-only and dense "
-                       "BMMC at each of 4, 8, 16 bytes per element; %d pass(es), "
-                       "%.1f s" % (n_sample, reps, dt))}
+    out = {"value": moved / dt / 1e9, "unit": "GB/s",
+           "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": ("C loop out[A x + c] = in[x] (OpenMP over x), 2^%d elements, "
+                      "one bit-reversal, half-swap, random BP, tiled-only and dense "
+                      "BMMC at each of 4, 8, 16 bytes per element; %d pass(es), "
+                      "%.1f s" % (n_sample, reps, dt)),
+           "cpu_model": cpu_model()}
+    # the same classes on one core, at 2^20 elements
+    small = oracle_sample(20)
+    bufs20 = {e: wl.payload(20, e) for e in (4, 8, 16)}
+    t0 = time.perf_counter()
+    moved = run_oracle_step(20, small, bufs20, threads=False)
+    out["single_thread"] = {"value": round(moved / (time.perf_counter() - t0) / 1e9, 3),
+                            "unit": "GB/s", "cores": 1,
+                            "sample": "the same 15 permutations at 2^20 elements"}
+    # the n = 20 configuration in full: int32 iota, bit-reversal + 16 dense
+    from oracle import f2
+    inv = lambda rows: f2.is_invertible(rows, len(rows))  # noqa: E731
+    c1 = [("bit_reverse", 4, wl.bit_reverse(20), 0)] + \
+        [("dense", 4) + tuple(wl.dense_bmmc(20, sd, inv)) for sd in range(1, 17)]
+    import numpy as np
+    iota = {4: np.arange(1 << 20, dtype=np.uint32)}
+    t0 = time.perf_counter()
+    moved = run_oracle_step(20, c1, iota)
+    out["n20_config"] = {"value": round(moved / (time.perf_counter() - t0) / 1e9, 3),
+                         "unit": "GB/s", "cores": oracle.num_threads(),
+                         "sample": "all 17 permutations of the n = 20 configuration"}
+    return out
 
 
 def reference_arm(args):
