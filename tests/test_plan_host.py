@@ -224,3 +224,20 @@ def test_bank_conflict_free_on_workloads(e):
             for ps in d["passes"]:
                 assert ps["wavefronts_load"] == ps["ideal_load"], d
                 assert ps["wavefronts_store"] == ps["ideal_store"], d
+
+
+def test_random_dense_factors_have_no_overlap():
+    """Sec. 6's observation: random dense matrices are (almost) never tiled,
+    and the tiled factors of their UL.P factorisation almost always have
+    n_over = 0 (their row bits avoid the segment bits)."""
+    n, e = 20, 4
+    overlaps, tiled = 0, 0
+    for s in range(60):
+        rows, c = wl.dense_bmmc(n, 900 + s, oracle_invertible)
+        p = bm.Plan(n, rows, c, e)
+        if p.num_passes == 1:
+            tiled += 1
+            continue
+        overlaps += sum(ps["n_over"] != 0 for ps in p.describe()["passes"])
+    assert tiled == 0
+    assert overlaps <= 3, overlaps  # at most 3 of 120 factor passes
