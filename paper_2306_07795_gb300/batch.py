@@ -7,6 +7,9 @@
 
 The tables and the two-pass workspace come from PyTorch's allocator and live
 as long as the Batch object; the library itself allocates nothing for a batch.
+Every array goes through the same passes as alone (Sec. 5.1 / 5.2); batching
+is this library's answer to the paper's remark that arrays under 2^20
+elements cannot fill a GPU (Sec. 6).
 """
 
 from . import _binding as B

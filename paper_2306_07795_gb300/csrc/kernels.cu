@@ -1,6 +1,7 @@
 // kernels.cu -- launcher of the tiled BMMC pass kernel for sm_103a.
 //
-// One thread block moves 2^it tiles of one pass; the body (cp.async tile
+// The tiled pass of Sec. 4.1-4.3 (the tiled BMMC of Sec. 5.1, and each of the
+// two passes of Sec. 5.2).  One thread block moves 2^it tiles of one pass; the body (cp.async tile
 // load into swizzled shared memory, barrier, 16-byte gathers and stores) is
 // dev::run_tile in tile_body.cuh, shared with the persistent batch kernel.
 // KEY selects an optional comparator epilogue (a column of compare-exchanges

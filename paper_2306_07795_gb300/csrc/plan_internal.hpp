@@ -1,4 +1,6 @@
-// plan_internal.hpp -- the plan object behind the opaque bmmc_plan handle.
+// plan_internal.hpp -- the plan object behind the opaque bmmc_plan handle:
+// the validated matrix (Sec. 3), its one or two tiled passes (Sec. 5.1, 5.2)
+// and each pass's launch tables (Sec. 4.1-4.3).
 #pragma once
 #include <stdint.h>
 

@@ -9,7 +9,8 @@
 // their events complete.  A request that finds nothing queued ahead of it and
 // the scheduler idle is admitted and launched in the submitting thread.  PLAIN
 // mode does planning, allocation and launch in the submitting thread on one
-// stream.
+// stream.  The paper has no serving counterpart (Sec. 6 times one array at a
+// time); every request runs the passes of Sec. 5.1 / 5.2 unchanged.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>

@@ -1,4 +1,8 @@
-"""Plan: a BMMC permutation bound to an array shape, callable on CUDA tensors."""
+"""Plan: a BMMC permutation bound to an array shape, callable on CUDA tensors.
+
+A plan is the paper's permutation out[A x + c] = in[x] (Sec. 3) after
+validation, classification and factorisation (Sec. 5.1, 5.2) into at most
+two tiled passes (Sec. 4), all done on the host by the C library."""
 
 from . import _binding as B
 

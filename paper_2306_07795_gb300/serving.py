@@ -8,6 +8,9 @@ the scheduling rules.
 
 drive(server, requests) submits each request at its arrival time (seconds
 from the start of the run) and returns per-request latencies.
+
+The paper has no serving counterpart (Sec. 6 times one array at a time);
+every request runs the same passes as a plain execution.
 """
 
 import time
