@@ -117,3 +117,33 @@ def test_sorting_network_graph_replay():
         graph.replay()
         torch.cuda.synchronize()
         assert torch.equal(out, torch.sort(x).values)
+
+
+@pytest.mark.parametrize("name,key,np_dtype", [KEYS[2], KEYS[1]])
+def test_execute_ce_full_size(name, key, np_dtype):
+    """A permute-and-compare pass at the benchmark's array size (n = 28 at 4
+    bytes, n = 27 at 8), dense matrix, both strategies: every element."""
+    import torch
+    e = np.dtype(np_dtype).itemsize
+    n = 28 if e == 4 else 27
+    rows, c = wl.dense_bmmc(n, 7, _inv)
+    arr = _values(np_dtype, 1 << n, 11)
+    want = _ce_ref(oracle.apply(n, rows, c, arr, elem_bytes=e))
+    x = torch.from_numpy(arr.view(np.int32 if e == 4 else np.int64).copy()).cuda()
+    for flags in (bm.BMMC_PLAN_PAPER, bm.BMMC_PLAN_SINGLE_PASS):
+        p = bm.Plan(n, rows, c, e, flags=flags)
+        y = torch.empty_like(x)
+        ws = torch.empty(max(p.workspace_bytes, 16), dtype=torch.uint8, device="cuda")
+        bm.bmmc_execute_ce(p.handle, x.data_ptr(), y.data_ptr(), ws.data_ptr(), key,
+                           torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy().view(np_dtype)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (name, flags)
+        del y, ws
+
+
+def test_sorting_network_n24():
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(24)
+    x = torch.randn(1 << 24, device="cuda", generator=g)
+    assert torch.equal(SortingNetwork(24)(x), torch.sort(x).values)
