@@ -866,8 +866,16 @@ def main():
                 "share_of_step": round(kernel_time[dom] / step_ms_sum, 4)}
     if traffic_note and traffic is None:
         roofline["traffic_note"] = traffic_note
+    # every kernel instantiation of the step against the same peak
+    kernels = {}
+    for k in sorted(kernel_time):
+        ms_l = kernel_time[k] / kernel_launches[k]
+        a = kernel_bytes[k] / kernel_launches[k] / (ms_l / 1e3) / 1e9
+        kernels[k] = {"achieved_gbs": round(a, 1), "frac_of_peak": round(a / peak, 4),
+                      "launches_per_step": kernel_launches[k],
+                      "share_of_step": round(kernel_time[k] / step_ms_sum, 4)}
 
-    extras = {}
+    extras = {"kernels": kernels}
     # ---- single-pass strategy on the dense set (beyond the paper) ---------
     if not args.no_extras and args.strategy == "paper":
         sp = {}
