@@ -22,6 +22,7 @@
 
 #include "bmmc.h"
 #include "bmmc_batch.h"
+#include "guard.hpp"
 #include "plan_internal.hpp"
 #include "tile_body.cuh"
 
@@ -277,6 +278,11 @@ size_t table_bytes(const bmmc_plan *plans, int count)
     return passes * kDescSlot + passes * sizeof(BatchEntry);
 }
 
+int batch_create_impl(bmmc_batch *out, const bmmc_plan *plans, int count,
+                      const void *const *ins, void *const *outs, void *ws, void *table,
+                      bmmc_stream_t stream);
+int batch_describe_impl(bmmc_batch b, char *buf, size_t len);
+
 }  // namespace
 
 extern "C" {
@@ -297,6 +303,47 @@ size_t bmmc_batch_table_bytes(const bmmc_plan *plans, int count)
 }
 
 int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
+                      const void *const *ins, void *const *outs, void *ws, void *table,
+                      bmmc_stream_t stream)
+{
+    return guarded(
+        [&] { return batch_create_impl(out, plans, count, ins, outs, ws, table, stream); });
+}
+
+int bmmc_batch_execute(bmmc_batch b, bmmc_stream_t stream)
+{
+    if (!b) return BMMC_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return BMMC_ERR_INVALID;
+    for (const Group &g : b->groups) {
+        cudaError_t err;
+        switch (g.e_log) {
+        case 2: err = launch_group<2>(g, b->dmem, (cudaStream_t)stream); break;
+        case 3: err = launch_group<3>(g, b->dmem, (cudaStream_t)stream); break;
+        default: err = launch_group<4>(g, b->dmem, (cudaStream_t)stream); break;
+        }
+        if (err != cudaSuccess) return BMMC_ERR_CUDA;
+    }
+    return BMMC_OK;
+}
+
+int bmmc_batch_num_launches(bmmc_batch b) { return b ? (int)b->groups.size() : BMMC_ERR_INVALID; }
+
+int bmmc_batch_describe(bmmc_batch b, char *buf, size_t len)
+{
+    return guarded([&] { return batch_describe_impl(b, buf, len); });
+}
+
+void bmmc_batch_destroy(bmmc_batch b)
+{
+    delete b;  // the table memory belongs to the caller
+}
+
+}  // extern "C"
+
+namespace {
+
+int batch_create_impl(bmmc_batch *out, const bmmc_plan *plans, int count,
                       const void *const *ins, void *const *outs, void *ws, void *table,
                       bmmc_stream_t stream)
 {
@@ -439,26 +486,7 @@ int bmmc_batch_create(bmmc_batch *out, const bmmc_plan *plans, int count,
     return BMMC_OK;
 }
 
-int bmmc_batch_execute(bmmc_batch b, bmmc_stream_t stream)
-{
-    if (!b) return BMMC_ERR_INVALID;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return BMMC_ERR_INVALID;
-    for (const Group &g : b->groups) {
-        cudaError_t err;
-        switch (g.e_log) {
-        case 2: err = launch_group<2>(g, b->dmem, (cudaStream_t)stream); break;
-        case 3: err = launch_group<3>(g, b->dmem, (cudaStream_t)stream); break;
-        default: err = launch_group<4>(g, b->dmem, (cudaStream_t)stream); break;
-        }
-        if (err != cudaSuccess) return BMMC_ERR_CUDA;
-    }
-    return BMMC_OK;
-}
-
-int bmmc_batch_num_launches(bmmc_batch b) { return b ? (int)b->groups.size() : BMMC_ERR_INVALID; }
-
-int bmmc_batch_describe(bmmc_batch b, char *buf, size_t len)
+int batch_describe_impl(bmmc_batch b, char *buf, size_t len)
 {
     if (!b) return BMMC_ERR_INVALID;
     std::string s = "{\"launches\": [";
@@ -483,9 +511,4 @@ int bmmc_batch_describe(bmmc_batch b, char *buf, size_t len)
     return (int)s.size();
 }
 
-void bmmc_batch_destroy(bmmc_batch b)
-{
-    delete b;  // the table memory belongs to the caller
-}
-
-}  // extern "C"
+}  // namespace

@@ -10,6 +10,7 @@
 #include "f2.hpp"
 #include "pass_desc.h"
 #include "plan.hpp"
+#include "guard.hpp"
 #include "plan_internal.hpp"
 
 namespace bmmc {
@@ -140,6 +141,9 @@ int execute_impl(bmmc_plan p, const void *in, void *out, void *ws, cudaStream_t 
     return err == cudaSuccess ? BMMC_OK : BMMC_ERR_CUDA;
 }
 
+int verify_impl(bmmc_plan p, uint64_t max_ctas);
+int describe_impl(bmmc_plan p, char *buf, size_t len);
+
 }  // namespace
 
 extern "C" {
@@ -147,13 +151,13 @@ extern "C" {
 int bmmc_plan_create(bmmc_plan *out, int n, const uint64_t *A_rows, uint64_t c,
                      size_t elem_bytes)
 {
-    return create_impl(out, n, A_rows, c, elem_bytes, nullptr);
+    return guarded([&] { return create_impl(out, n, A_rows, c, elem_bytes, nullptr); });
 }
 
 int bmmc_plan_create_ex(bmmc_plan *out, int n, const uint64_t *A_rows, uint64_t c,
                         size_t elem_bytes, const bmmc_plan_options *opts)
 {
-    return create_impl(out, n, A_rows, c, elem_bytes, opts);
+    return guarded([&] { return create_impl(out, n, A_rows, c, elem_bytes, opts); });
 }
 
 void bmmc_plan_destroy(bmmc_plan p)
@@ -198,7 +202,9 @@ int bmmc_plan_inverse(bmmc_plan p, bmmc_plan *out)
     o.seg_bits = p->opt.seg_bits;
     o.cta_tile_log2 = p->opt.cta_tile_log2;
     o.tile_order = p->opt.tile_order;
-    return create_impl(out, p->n, inv.r, inv.apply(p->c), (size_t)1 << p->e_log, &o);
+    return guarded([&] {
+        return create_impl(out, p->n, inv.r, inv.apply(p->c), (size_t)1 << p->e_log, &o);
+    });
 }
 
 int bmmc_plan_compose(bmmc_plan second, bmmc_plan first, bmmc_plan *out)
@@ -216,7 +222,9 @@ int bmmc_plan_compose(bmmc_plan second, bmmc_plan first, bmmc_plan *out)
     o.seg_bits = second->opt.seg_bits;
     o.cta_tile_log2 = second->opt.cta_tile_log2;
     o.tile_order = second->opt.tile_order;
-    return create_impl(out, second->n, a.r, c, (size_t)1 << second->e_log, &o);
+    return guarded([&] {
+        return create_impl(out, second->n, a.r, c, (size_t)1 << second->e_log, &o);
+    });
 }
 
 int bmmc_parm_matrix(int n, uint64_t mask, uint64_t *rows_out)
@@ -301,6 +309,20 @@ int bmmc_execute_ce(bmmc_plan p, const void *in, void *out, void *ws, int key_ty
 
 int bmmc_plan_verify(bmmc_plan p, uint64_t max_ctas)
 {
+    return guarded([&] { return verify_impl(p, max_ctas); });
+}
+
+int bmmc_plan_describe(bmmc_plan p, char *buf, size_t len)
+{
+    return guarded([&] { return describe_impl(p, buf, len); });
+}
+
+}  // extern "C"
+
+namespace {
+
+int verify_impl(bmmc_plan p, uint64_t max_ctas)
+{
     if (!p) return BMMC_ERR_INVALID;
     for (int i = 0; i < p->npass; ++i) {
         std::string why;
@@ -324,7 +346,7 @@ int bmmc_plan_verify(bmmc_plan p, uint64_t max_ctas)
     return BMMC_OK;
 }
 
-int bmmc_plan_describe(bmmc_plan p, char *buf, size_t len)
+int describe_impl(bmmc_plan p, char *buf, size_t len)
 {
     if (!p) return BMMC_ERR_INVALID;
     std::string s = "{\"n\": " + std::to_string(p->n) +
@@ -358,6 +380,10 @@ int bmmc_plan_describe(bmmc_plan p, char *buf, size_t len)
     }
     return (int)s.size();
 }
+
+}  // namespace
+
+extern "C" {
 
 const char *bmmc_strerror(int code)
 {

@@ -542,127 +542,139 @@ extern "C" {
 
 int bmmc_server_create(bmmc_server *out, const bmmc_server_config *cfg)
 {
-    if (!out || !cfg) return BMMC_ERR_INVALID;
-    *out = nullptr;
-    for (int r : cfg->reserved)
-        if (r) return BMMC_ERR_UNSUPPORTED;
-    if (cfg->mode != BMMC_SERVER_CONTINUOUS && cfg->mode != BMMC_SERVER_PLAIN)
-        return BMMC_ERR_UNSUPPORTED;
-    if (cfg->streams < 1 || cfg->streams > kMaxStreams) return BMMC_ERR_UNSUPPORTED;
-    if (cfg->arena_bytes < kAlign || cfg->budget_bytes == 0) return BMMC_ERR_UNSUPPORTED;
-    if (cfg->plan_flags > BMMC_PLAN_SINGLE_PASS) return BMMC_ERR_UNSUPPORTED;
-    if (cfg->plan_cache < 0) return BMMC_ERR_UNSUPPORTED;
-    bmmc_server_s *s = new (std::nothrow) bmmc_server_s();
-    if (!s) return BMMC_ERR_OOM;
-    s->cfg = *cfg;
-    s->nstreams = cfg->mode == BMMC_SERVER_PLAIN ? 1 : cfg->streams;
-    if (cudaGetDevice(&s->device) != cudaSuccess) {
-        delete s;
-        return BMMC_ERR_CUDA;
-    }
-    if (cudaMalloc((void **)&s->arena_mem, cfg->arena_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        delete s;
+    try {
+        if (!out || !cfg) return BMMC_ERR_INVALID;
+        *out = nullptr;
+        for (int r : cfg->reserved)
+            if (r) return BMMC_ERR_UNSUPPORTED;
+        if (cfg->mode != BMMC_SERVER_CONTINUOUS && cfg->mode != BMMC_SERVER_PLAIN)
+            return BMMC_ERR_UNSUPPORTED;
+        if (cfg->streams < 1 || cfg->streams > kMaxStreams) return BMMC_ERR_UNSUPPORTED;
+        if (cfg->arena_bytes < kAlign || cfg->budget_bytes == 0) return BMMC_ERR_UNSUPPORTED;
+        if (cfg->plan_flags > BMMC_PLAN_SINGLE_PASS) return BMMC_ERR_UNSUPPORTED;
+        if (cfg->plan_cache < 0) return BMMC_ERR_UNSUPPORTED;
+        bmmc_server_s *s = new (std::nothrow) bmmc_server_s();
+        if (!s) return BMMC_ERR_OOM;
+        s->cfg = *cfg;
+        s->nstreams = cfg->mode == BMMC_SERVER_PLAIN ? 1 : cfg->streams;
+        if (cudaGetDevice(&s->device) != cudaSuccess) {
+            delete s;
+            return BMMC_ERR_CUDA;
+        }
+        if (cudaMalloc((void **)&s->arena_mem, cfg->arena_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return BMMC_ERR_OOM;
+        }
+        s->arena.init(s->arena_mem, cfg->arena_bytes);
+        for (int i = 0; i < s->nstreams; ++i)
+            cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) == cudaSuccess) s->events.push_back(e);
+        }
+        cudaEventCreate(&s->start);
+        cudaDeviceSynchronize();
+        cudaEventRecord(s->start, s->streams[0]);
+        cudaEventSynchronize(s->start);
+        s->t0 = std::chrono::steady_clock::now();
+        if (cudaGetLastError() != cudaSuccess) {
+            bmmc_server_destroy(s);
+            return BMMC_ERR_CUDA;
+        }
+        if (cfg->mode == BMMC_SERVER_CONTINUOUS) s->worker = std::thread(worker_main, s);
+        *out = s;
+        return BMMC_OK;
+    } catch (const std::bad_alloc &) {
         return BMMC_ERR_OOM;
+    } catch (...) {
+        return BMMC_ERR_INVALID;
     }
-    s->arena.init(s->arena_mem, cfg->arena_bytes);
-    for (int i = 0; i < s->nstreams; ++i)
-        cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
-    for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) == cudaSuccess) s->events.push_back(e);
-    }
-    cudaEventCreate(&s->start);
-    cudaDeviceSynchronize();
-    cudaEventRecord(s->start, s->streams[0]);
-    cudaEventSynchronize(s->start);
-    s->t0 = std::chrono::steady_clock::now();
-    if (cudaGetLastError() != cudaSuccess) {
-        bmmc_server_destroy(s);
-        return BMMC_ERR_CUDA;
-    }
-    if (cfg->mode == BMMC_SERVER_CONTINUOUS) s->worker = std::thread(worker_main, s);
-    *out = s;
-    return BMMC_OK;
 }
 
 int bmmc_server_submit(bmmc_server s, uint64_t id, int n, const uint64_t *A_rows, uint64_t c,
                        size_t elem_bytes, const void *in)
 {
-    if (!s || !in) return BMMC_ERR_INVALID;
-    if ((uintptr_t)in & 15u) return BMMC_ERR_ALIGN;
-    Req *r = new (std::nothrow) Req();
-    if (!r) return BMMC_ERR_OOM;
-    r->id = id;
-    r->in = in;
-    r->submit_ms = s->now_ms();
-    int rc = prepare(s, r, n, A_rows, c, elem_bytes);
-    if (rc != BMMC_OK) {
-        delete r;
-        return rc;
-    }
-    if (s->cfg.mode == BMMC_SERVER_CONTINUOUS) {
-        auto enqueue = [s, r]() {
+    try {
+        if (!s || !in) return BMMC_ERR_INVALID;
+        if ((uintptr_t)in & 15u) return BMMC_ERR_ALIGN;
+        Req *r = new (std::nothrow) Req();
+        if (!r) return BMMC_ERR_OOM;
+        r->id = id;
+        r->in = in;
+        r->submit_ms = s->now_ms();
+        int rc = prepare(s, r, n, A_rows, c, elem_bytes);
+        if (rc != BMMC_OK) {
+            delete r;
+            return rc;
+        }
+        if (s->cfg.mode == BMMC_SERVER_CONTINUOUS) {
+            auto enqueue = [s, r]() {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->submitted.push_back(r);
+                s->cv.notify_one();
+                return BMMC_OK;
+            };
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->outstanding += 1;
+                s->n_submitted += 1;
+                if (s->hold || s->stop || !s->submitted.empty()) {
+                    s->submitted.push_back(r);
+                    s->cv.notify_one();
+                    return BMMC_OK;
+                }
+            }
+            // Inline dispatch: when nothing submitted earlier is still queued
+            // and the scheduler is not busy, admit and launch in this thread, as
+            // the plain loop would, instead of waking the scheduler.  Requests
+            // taken by the scheduler but not yet queued (in_transit) keep their
+            // place: this one then queues behind them.
+            std::unique_lock<std::mutex> lk2(s->sched_mu, std::try_to_lock);
+            if (!lk2.owns_lock() || s->in_transit.load() != 0) {
+                if (lk2.owns_lock()) lk2.unlock();
+                return enqueue();
+            }
+            bool launched = false;
+            if (s->waiting.empty()) {
+                const int prev = enter_device(s);
+                retire(s);
+                launched = admit_one(s, r);
+                if (prev >= 0) cudaSetDevice(prev);
+            }
+            if (!launched) s->waiting.push_back(r);
+            if (launched) s->n_inline += 1;
+            lk2.unlock();
             std::lock_guard<std::mutex> lk(s->mu);
-            s->submitted.push_back(r);
-            s->cv.notify_one();
+            s->cv.notify_one();  // the scheduler retires the launch, or admits r
             return BMMC_OK;
-        };
+        }
+        // PLAIN: allocate (waiting for completions if the arena is full), launch.
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->outstanding += 1;
             s->n_submitted += 1;
-            if (s->hold || s->stop || !s->submitted.empty()) {
-                s->submitted.push_back(r);
-                s->cv.notify_one();
-                return BMMC_OK;
-            }
         }
-        // Inline dispatch: when nothing submitted earlier is still queued
-        // and the scheduler is not busy, admit and launch in this thread, as
-        // the plain loop would, instead of waking the scheduler.  Requests
-        // taken by the scheduler but not yet queued (in_transit) keep their
-        // place: this one then queues behind them.
-        std::unique_lock<std::mutex> lk2(s->sched_mu, std::try_to_lock);
-        if (!lk2.owns_lock() || s->in_transit.load() != 0) {
-            if (lk2.owns_lock()) lk2.unlock();
-            return enqueue();
-        }
-        bool launched = false;
-        if (s->waiting.empty()) {
-            const int prev = enter_device(s);
-            retire(s);
-            launched = admit_one(s, r);
-            if (prev >= 0) cudaSetDevice(prev);
-        }
-        if (!launched) s->waiting.push_back(r);
-        if (launched) s->n_inline += 1;
-        lk2.unlock();
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->cv.notify_one();  // the scheduler retires the launch, or admits r
-        return BMMC_OK;
-    }
-    // PLAIN: allocate (waiting for completions if the arena is full), launch.
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->outstanding += 1;
-        s->n_submitted += 1;
-    }
-    std::lock_guard<std::mutex> lk(s->sched_mu);
-    retire(s);
-    while (!allocate(s, r)) {
-        if (s->inflight[0].empty()) {  // cannot happen: prepare checked the size
-            release_plan(s, r);
-            delete r;
-            return BMMC_ERR_OOM;
-        }
-        cudaEventSynchronize(s->inflight[0].front().ev);
+        std::lock_guard<std::mutex> lk(s->sched_mu);
         retire(s);
+        while (!allocate(s, r)) {
+            if (s->inflight[0].empty()) {  // cannot happen: prepare checked the size
+                release_plan(s, r);
+                delete r;
+                return BMMC_ERR_OOM;
+            }
+            cudaEventSynchronize(s->inflight[0].front().ev);
+            retire(s);
+        }
+        s->used += r->bytes;
+        launch_single(s, r, 0);
+        note_peaks(s);
+        return BMMC_OK;
+    } catch (const std::bad_alloc &) {
+        return BMMC_ERR_OOM;
+    } catch (...) {
+        return BMMC_ERR_INVALID;
     }
-    s->used += r->bytes;
-    launch_single(s, r, 0);
-    note_peaks(s);
-    return BMMC_OK;
 }
 
 int bmmc_server_drain(bmmc_server s)
@@ -695,12 +707,18 @@ double bmmc_server_now_ms(bmmc_server s) { return s ? s->now_ms() : -1.0; }
 
 int bmmc_server_results(bmmc_server s, bmmc_server_result *res, int max)
 {
-    if (!s || (!res && max > 0) || max < 0) return BMMC_ERR_INVALID;
-    std::lock_guard<std::mutex> lk(s->mu);
-    int k = (int)std::min<size_t>((size_t)max, s->results.size());
-    for (int i = 0; i < k; ++i) res[i] = s->results[i];
-    s->results.erase(s->results.begin(), s->results.begin() + k);
-    return k;
+    try {
+        if (!s || (!res && max > 0) || max < 0) return BMMC_ERR_INVALID;
+        std::lock_guard<std::mutex> lk(s->mu);
+        int k = (int)std::min<size_t>((size_t)max, s->results.size());
+        for (int i = 0; i < k; ++i) res[i] = s->results[i];
+        s->results.erase(s->results.begin(), s->results.begin() + k);
+        return k;
+    } catch (const std::bad_alloc &) {
+        return BMMC_ERR_OOM;
+    } catch (...) {
+        return BMMC_ERR_INVALID;
+    }
 }
 
 int bmmc_server_release(bmmc_server s, void *out)
@@ -716,48 +734,54 @@ int bmmc_server_release(bmmc_server s, void *out)
 
 int bmmc_server_stats(bmmc_server s, char *buf, size_t len)
 {
-    if (!s) return BMMC_ERR_INVALID;
-    char tmp[768];
-    uint64_t single, inl, groups, grouped, peak_b, peak_i, sub, comp, hits, cached;
-    {
-        std::lock_guard<std::mutex> lk(s->sched_mu);
-        single = s->n_single;
-        inl = s->n_inline;
-        groups = s->n_groups;
-        grouped = s->n_grouped;
-        peak_b = s->peak_bytes;
-        peak_i = s->peak_inflight;
+    try {
+        if (!s) return BMMC_ERR_INVALID;
+        char tmp[768];
+        uint64_t single, inl, groups, grouped, peak_b, peak_i, sub, comp, hits, cached;
+        {
+            std::lock_guard<std::mutex> lk(s->sched_mu);
+            single = s->n_single;
+            inl = s->n_inline;
+            groups = s->n_groups;
+            grouped = s->n_grouped;
+            peak_b = s->peak_bytes;
+            peak_i = s->peak_inflight;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            sub = s->n_submitted;
+            comp = s->n_completed;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->plan_mu);
+            hits = s->n_plan_hits;
+            cached = s->plans.size();
+        }
+        int k = snprintf(tmp, sizeof(tmp),
+                         "{\"mode\": \"%s\", \"streams\": %d, \"submitted\": %llu, "
+                         "\"completed\": %llu, \"single_launches\": %llu, "
+                         "\"inline_launches\": %llu, "
+                         "\"group_launches\": %llu, \"grouped_requests\": %llu, "
+                         "\"peak_bytes_in_flight\": %llu, \"peak_requests_in_flight\": %llu, "
+                         "\"plan_cache_hits\": %llu, \"plans_cached\": %llu}",
+                         s->cfg.mode == BMMC_SERVER_PLAIN ? "plain" : "continuous", s->nstreams,
+                         (unsigned long long)sub, (unsigned long long)comp,
+                         (unsigned long long)single, (unsigned long long)inl,
+                         (unsigned long long)groups,
+                         (unsigned long long)grouped, (unsigned long long)peak_b,
+                         (unsigned long long)peak_i, (unsigned long long)hits,
+                         (unsigned long long)cached);
+        if (buf && len) {
+            size_t cpy = (size_t)k < len - 1 ? (size_t)k : len - 1;
+            memcpy(buf, tmp, cpy);
+            buf[cpy] = 0;
+        }
+        return k;
+    } catch (const std::bad_alloc &) {
+        return BMMC_ERR_OOM;
+    } catch (...) {
+        return BMMC_ERR_INVALID;
     }
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        sub = s->n_submitted;
-        comp = s->n_completed;
-    }
-    {
-        std::lock_guard<std::mutex> lk(s->plan_mu);
-        hits = s->n_plan_hits;
-        cached = s->plans.size();
-    }
-    int k = snprintf(tmp, sizeof(tmp),
-                     "{\"mode\": \"%s\", \"streams\": %d, \"submitted\": %llu, "
-                     "\"completed\": %llu, \"single_launches\": %llu, "
-                     "\"inline_launches\": %llu, "
-                     "\"group_launches\": %llu, \"grouped_requests\": %llu, "
-                     "\"peak_bytes_in_flight\": %llu, \"peak_requests_in_flight\": %llu, "
-                     "\"plan_cache_hits\": %llu, \"plans_cached\": %llu}",
-                     s->cfg.mode == BMMC_SERVER_PLAIN ? "plain" : "continuous", s->nstreams,
-                     (unsigned long long)sub, (unsigned long long)comp,
-                     (unsigned long long)single, (unsigned long long)inl,
-                     (unsigned long long)groups,
-                     (unsigned long long)grouped, (unsigned long long)peak_b,
-                     (unsigned long long)peak_i, (unsigned long long)hits,
-                     (unsigned long long)cached);
-    if (buf && len) {
-        size_t cpy = (size_t)k < len - 1 ? (size_t)k : len - 1;
-        memcpy(buf, tmp, cpy);
-        buf[cpy] = 0;
-    }
-    return k;
 }
 
 void bmmc_server_destroy(bmmc_server s)
