@@ -151,7 +151,16 @@ def _check(code, what):
 
 
 def _rows(rows):
+    """Row masks as a C uint64 array (an array already converted is passed
+    through, so callers on a hot path can convert once)."""
+    if isinstance(rows, ctypes.Array):
+        return rows
     return (ctypes.c_uint64 * max(1, len(rows)))(*[int(r) for r in rows])
+
+
+def rows_array(rows):
+    """Convert row masks once for repeated calls (see _rows)."""
+    return _rows(rows)
 
 
 # ---------------------------------------------------------------------------
