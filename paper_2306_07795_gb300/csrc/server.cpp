@@ -429,12 +429,14 @@ int enter_device(const bmmc_server_s *s)
 void worker_main(bmmc_server_s *s)
 {
     cudaSetDevice(s->device);
+    // Requests taken from `submitted` and not yet queued in `waiting`; kept
+    // across turns so that a failed host allocation loses none of them.
+    std::deque<Req *> fresh;
     for (;;) {
-        std::deque<Req *> fresh;
         bool busy;
         {
             std::lock_guard<std::mutex> lk2(s->sched_mu);
-            busy = !s->waiting.empty() || s->n_inflight != 0;
+            busy = !s->waiting.empty() || s->n_inflight != 0 || !fresh.empty();
         }
         {
             std::unique_lock<std::mutex> lk(s->mu);
@@ -448,15 +450,26 @@ void worker_main(bmmc_server_s *s)
                     continue;
                 }
             }
-            fresh.swap(s->submitted);
+            if (fresh.empty()) fresh.swap(s->submitted);
             s->in_transit.store(fresh.size());
         }
         std::lock_guard<std::mutex> lk2(s->sched_mu);
-        for (Req *r : fresh) s->waiting.push_back(r);
-        s->in_transit.store(0);
-        bool progress = retire(s);
-        progress |= admit(s);
-        if (!progress && s->n_inflight) std::this_thread::yield();
+        try {
+            while (!fresh.empty()) {
+                s->waiting.push_back(fresh.front());
+                fresh.pop_front();
+            }
+            s->in_transit.store(0);
+            bool progress = retire(s);
+            progress |= admit(s);
+            if (!progress && s->n_inflight) std::this_thread::yield();
+        } catch (const std::bad_alloc &) {
+            // Host memory ran out while queueing or admitting: what is not
+            // queued yet stays in `fresh` (still counted in transit, so no
+            // later request overtakes it) and the next turn retries, instead
+            // of this thread ending the process.
+            std::this_thread::yield();
+        }
     }
 }
 
