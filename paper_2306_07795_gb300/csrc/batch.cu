@@ -56,19 +56,30 @@ constexpr uint32_t kMaxSlots = 3;
 template <int E_LOG>
 __global__ void __launch_bounds__(kThreads, 4)
     bmmc_batch_pass(const BatchEntry *__restrict__ ent, uint32_t count, uint32_t total,
-                    const uint8_t *__restrict__ descs, uint32_t tile_bytes, uint32_t slots)
+                    const uint8_t *__restrict__ descs, uint32_t tile_bytes, uint32_t slots,
+                    uint32_t chunk)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t tid = threadIdx.x;
 
-    // Block b takes the contiguous range [b * per, (b + 1) * per) of the
-    // items.  (Striding over the items by the grid size measured 6% slower on
-    // a batch of 4096 arrays of 2^10..2^24 elements.)
-    const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
-    const uint32_t begin = blockIdx.x * per;
-    if (begin >= total) return;
-    const uint32_t end = total - begin > per ? begin + per : total;
+    // The items are cut into chunks of `chunk` consecutive items; block b
+    // takes chunks b, b + G, b + 2G, ... (G blocks).  A chunk of ceil(total /
+    // G) items gives each block one contiguous range.
+    uint32_t cid = blockIdx.x;
+    if ((uint64_t)cid * chunk >= total) return;
+    const uint32_t begin = cid * chunk;
+    uint32_t cend = total - begin > chunk ? begin + chunk : total;
+    // the item after `it` for this block (total when there is none); moves
+    // *c and *e to the next chunk when `it` ends the current one
+    auto advance = [&](uint32_t it, uint32_t *c, uint32_t *e) -> uint32_t {
+        if (it + 1 < *e) return it + 1;
+        const uint64_t start = (uint64_t)(*c + gridDim.x) * chunk;
+        if (start >= total) return total;
+        *c += gridDim.x;
+        *e = total - (uint32_t)start > chunk ? (uint32_t)start + chunk : total;
+        return (uint32_t)start;
+    };
     // Launched with programmatic stream serialization (phase 2 is scheduled
     // while phase 1 drains); nothing above touched global memory.
     dev::grid_dependency_wait();
@@ -142,12 +153,13 @@ __global__ void __launch_bounds__(kThreads, 4)
     stage(begin, 0, &a_cur);
     issue(begin, a_cur, 0);
     int slot = 0;
-    for (uint32_t item = begin; item < end; ++item) {
+    for (uint32_t item = begin; item < total;) {
         const int next = slot + 1 == (int)slots ? 0 : slot + 1;
         uint32_t a_next = a_cur;
-        if (item + 1 < end) {
-            stage(item + 1, next, &a_next);
-            issue(item + 1, a_next, next);
+        const uint32_t nxt = advance(item, &cid, &cend);
+        if (nxt < total) {
+            stage(nxt, next, &a_next);
+            issue(nxt, a_next, next);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -163,6 +175,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         if (slots == 2) __syncthreads();  // buffer `slot` is free for item + 2
         a_cur = a_next;
         slot = next;
+        item = nxt;
     }
 }
 
@@ -175,6 +188,7 @@ struct Group {
     uint32_t smem = 0;
     uint32_t tile_bytes = 0;  // largest tile buffer of the group's passes
     uint32_t slots = 0;       // tile buffers (3, or 2 when 3 do not fit)
+    uint32_t chunk = 0;       // consecutive items a block takes at a time
     uint32_t grid = 0;
     uint32_t arrays = 0;
 };
@@ -194,7 +208,8 @@ cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, bmmc_batch_pass<E_LOG>, ent, g.count, (uint32_t)g.total,
-                              static_cast<const uint8_t *>(dmem), g.tile_bytes, g.slots);
+                              static_cast<const uint8_t *>(dmem), g.tile_bytes, g.slots,
+                              g.chunk);
 }
 
 // Shared memory of a group with `slots` tile buffers.
@@ -232,6 +247,16 @@ cudaError_t prepare_group(Group *g, int sms)
     uint64_t grid = (uint64_t)sms * (uint64_t)per_sm;
     if (grid > g->total) grid = g->total;
     g->grid = (uint32_t)grid;
+    // Chunks of about 1/64 of a block's share of the items, at least 16: the
+    // blocks resident at a time then work on nearby tiles, while a block
+    // still reloads tables rarely.  (On 128 arrays of 2^10..2^24 elements
+    // this measured 3-5 % faster than one contiguous range per block, and
+    // within 1 % of it on 4096 arrays; chunks of 4 items lost 7 % there.)
+    const uint64_t per = (g->total + grid - 1) / grid;
+    uint64_t chunk = per / 64;
+    if (chunk < 16) chunk = 16;
+    if (chunk > per) chunk = per;
+    g->chunk = (uint32_t)chunk;
     return cudaSuccess;
 }
 
