@@ -53,3 +53,17 @@ def test_two_rank_replicas_gloo():
     rows0, rows1 = results[0][3], results[1][3]
     assert rows0[:2] == rows1[:2]
     assert rows0[2:] != rows1[2:]
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """Under torchrun only rank 0 times the oracle and prints; the other
+    ranks exit at once with status 0."""
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    import sys
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1",
+                                      "--warmup", "0"])
+    args = bench.parse_args()
+    assert bench.reference_arm(args) == 0
+    assert capsys.readouterr().out == ""
