@@ -77,6 +77,19 @@ int bmmc_batch_describe(bmmc_batch b, char *buf, size_t len);
  * be reused once no launch of the batch is still running. */
 void bmmc_batch_destroy(bmmc_batch b);
 
+/*
+ * One-shot form: run plans[i] on ins[i] -> outs[i] for i < count as one batch
+ * on `stream`, with the tables and the two-pass workspace taken from the
+ * stream-ordered allocator (cudaMallocAsync) and given back (cudaFreeAsync)
+ * on the same stream, so the call never synchronises the device.  Equivalent
+ * to create, execute and destroy with memory that lives exactly as long as
+ * the launches; use bmmc_batch_create for repeated executions or graphs.
+ * Conventions and errors as for bmmc_batch_create and bmmc_batch_execute
+ * (OOM when the stream-ordered allocation fails).
+ */
+int bmmc_execute_batch(const bmmc_plan *plans, const void *const *ins, void *const *outs,
+                       int count, bmmc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,7 @@ EXPORTED = (
     "bmmc_batch_workspace_bytes", "bmmc_batch_table_bytes", "bmmc_batch_create",
     "bmmc_batch_execute",
     "bmmc_batch_num_launches", "bmmc_batch_describe", "bmmc_batch_destroy",
+    "bmmc_execute_batch",
     # include/bmmc_server.h
     "bmmc_server_create", "bmmc_server_submit", "bmmc_server_drain",
     "bmmc_server_results", "bmmc_server_release", "bmmc_server_stats",
@@ -124,6 +125,7 @@ def lib():
         "bmmc_batch_num_launches": (ctypes.c_int, [vp]),
         "bmmc_batch_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_batch_destroy": (None, [vp]),
+        "bmmc_execute_batch": (ctypes.c_int, [vpp, vpp, vpp, ctypes.c_int, vp]),
         "bmmc_server_create": (ctypes.c_int, [ctypes.POINTER(vp),
                                               ctypes.POINTER(bmmc_server_config)]),
         "bmmc_server_submit": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int, u64p,
@@ -319,6 +321,12 @@ def bmmc_batch_describe(h):
 
 def bmmc_batch_destroy(h):
     lib().bmmc_batch_destroy(h)
+
+
+def bmmc_execute_batch(plan_handles, in_ptrs, out_ptrs, stream=0):
+    _check(lib().bmmc_execute_batch(_ptr_array(plan_handles), _ptr_array(in_ptrs),
+                                    _ptr_array(out_ptrs), len(plan_handles), stream),
+           "bmmc_execute_batch")
 
 
 # ---------------------------------------------------------------------------

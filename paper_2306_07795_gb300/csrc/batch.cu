@@ -364,6 +364,34 @@ void bmmc_batch_destroy(bmmc_batch b)
     delete b;  // the table memory belongs to the caller
 }
 
+int bmmc_execute_batch(const bmmc_plan *plans, const void *const *ins, void *const *outs,
+                       int count, bmmc_stream_t stream)
+{
+    if (!plans || !ins || !outs || count <= 0) return BMMC_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ws_bytes = bmmc_batch_workspace_bytes(plans, count);
+    const size_t tab_bytes = bmmc_batch_table_bytes(plans, count);
+    if (!tab_bytes) return BMMC_ERR_INVALID;
+    void *table = nullptr, *ws = nullptr;
+    if (cudaMallocAsync(&table, tab_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return BMMC_ERR_OOM;
+    }
+    if (ws_bytes && cudaMallocAsync(&ws, ws_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(table, s);
+        return BMMC_ERR_OOM;
+    }
+    bmmc_batch b = nullptr;
+    int rc = bmmc_batch_create(&b, plans, count, ins, outs, ws, table, stream);
+    if (rc == BMMC_OK) rc = bmmc_batch_execute(b, stream);
+    bmmc_batch_destroy(b);
+    // stream order frees the memory after the launches
+    if (ws) cudaFreeAsync(ws, s);
+    cudaFreeAsync(table, s);
+    return rc;
+}
+
 }  // extern "C"
 
 namespace {

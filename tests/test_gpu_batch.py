@@ -190,3 +190,23 @@ def test_batched_config_full_size(flags):
             got = y[torch.from_numpy(ys.astype(np.int64)).cuda()].cpu().numpy()
             want = xs.astype(np.int64).astype(np.int32) | np.int32(tag)
             assert np.array_equal(got, want), (i, n)
+
+
+def test_one_shot_execute_batch():
+    """bmmc_execute_batch: stream-ordered tables and workspace, same results
+    as the batch object, on a side stream, repeated without synchronising."""
+    import torch
+    ns = [9, 12, 15, 17, 20, 11]
+    es = [4, 8, 16, 4, 8, 4]
+    for flags in (bm.BMMC_PLAN_PAPER, bm.BMMC_PLAN_SINGLE_PASS):
+        plans, ins, outs, host = _build(ns, es, flags, seed0=70)
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        for _ in range(3):
+            bm.bmmc_execute_batch([p.handle for p in plans], [x.data_ptr() for x in ins],
+                                  [y.data_ptr() for y in outs], st.cuda_stream)
+        st.synchronize()
+        _check(outs, host)
+    with pytest.raises(bm.BmmcError) as ei:
+        bm.bmmc_execute_batch([], [], [], 0)
+    assert ei.value.code == bm.BMMC_ERR_INVALID
