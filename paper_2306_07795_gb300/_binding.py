@@ -39,6 +39,8 @@ EXPORTED = (
     "bmmc_batch_execute",
     "bmmc_batch_num_launches", "bmmc_batch_describe", "bmmc_batch_destroy",
     "bmmc_execute_batch",
+    # include/bmmc_debug.h
+    "bmmc_debug_fail_allocs", "bmmc_debug_fail_launches",
     # include/bmmc_server.h
     "bmmc_server_create", "bmmc_server_submit", "bmmc_server_drain",
     "bmmc_server_results", "bmmc_server_release", "bmmc_server_stats",
@@ -126,6 +128,8 @@ def lib():
         "bmmc_batch_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_batch_destroy": (None, [vp]),
         "bmmc_execute_batch": (ctypes.c_int, [vpp, vpp, vpp, ctypes.c_int, vp]),
+        "bmmc_debug_fail_allocs": (None, [ctypes.c_int]),
+        "bmmc_debug_fail_launches": (None, [ctypes.c_int]),
         "bmmc_server_create": (ctypes.c_int, [ctypes.POINTER(vp),
                                               ctypes.POINTER(bmmc_server_config)]),
         "bmmc_server_submit": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int, u64p,
@@ -321,6 +325,14 @@ def bmmc_batch_describe(h):
 
 def bmmc_batch_destroy(h):
     lib().bmmc_batch_destroy(h)
+
+
+def bmmc_debug_fail_allocs(count):
+    lib().bmmc_debug_fail_allocs(int(count))
+
+
+def bmmc_debug_fail_launches(count):
+    lib().bmmc_debug_fail_launches(int(count))
 
 
 def bmmc_execute_batch(plan_handles, in_ptrs, out_ptrs, stream=0):

@@ -22,6 +22,7 @@
 
 #include "bmmc.h"
 #include "bmmc_batch.h"
+#include "debug_hooks.hpp"
 #include "guard.hpp"
 #include "plan_internal.hpp"
 #include "tile_body.cuh"
@@ -341,6 +342,7 @@ int bmmc_batch_execute(bmmc_batch b, bmmc_stream_t stream)
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return BMMC_ERR_INVALID;
     for (const Group &g : b->groups) {
+        if (debug_fail_launch()) return BMMC_ERR_CUDA;
         cudaError_t err;
         switch (g.e_log) {
         case 2: err = launch_group<2>(g, b->dmem, (cudaStream_t)stream); break;
@@ -373,6 +375,7 @@ int bmmc_execute_batch(const bmmc_plan *plans, const void *const *ins, void *con
     const size_t tab_bytes = bmmc_batch_table_bytes(plans, count);
     if (!tab_bytes) return BMMC_ERR_INVALID;
     void *table = nullptr, *ws = nullptr;
+    if (debug_fail_alloc()) return BMMC_ERR_OOM;
     if (cudaMallocAsync(&table, tab_bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return BMMC_ERR_OOM;

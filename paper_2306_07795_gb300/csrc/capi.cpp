@@ -10,6 +10,7 @@
 #include "f2.hpp"
 #include "pass_desc.h"
 #include "plan.hpp"
+#include "debug_hooks.hpp"
 #include "guard.hpp"
 #include "plan_internal.hpp"
 
@@ -129,14 +130,17 @@ int execute_impl(bmmc_plan p, const void *in, void *out, void *ws, cudaStream_t 
     if (((uintptr_t)in | (uintptr_t)out) & 15u) return BMMC_ERR_ALIGN;
     if (overlap(in, out, bytes)) return BMMC_ERR_ALIAS;
     if (p->npass == 1) {
+        if (debug_fail_launch()) return BMMC_ERR_CUDA;
         cudaError_t err = launch_pass(p->desc[0], in, out, s, key);
         return err == cudaSuccess ? BMMC_OK : BMMC_ERR_CUDA;
     }
     if (!ws) return BMMC_ERR_INVALID;
     if ((uintptr_t)ws & 15u) return BMMC_ERR_ALIGN;
     if (overlap(ws, in, bytes) || overlap(ws, out, bytes)) return BMMC_ERR_ALIAS;
+    if (debug_fail_launch()) return BMMC_ERR_CUDA;
     cudaError_t err = launch_pass(p->desc[0], in, ws, s, 0);
     if (err != cudaSuccess) return BMMC_ERR_CUDA;
+    if (debug_fail_launch()) return BMMC_ERR_CUDA;
     err = launch_pass(p->desc[1], ws, out, s, key);
     return err == cudaSuccess ? BMMC_OK : BMMC_ERR_CUDA;
 }
@@ -257,6 +261,7 @@ int bmmc_execute(bmmc_plan p, const void *in, void *out, bmmc_stream_t stream)
         std::lock_guard<std::mutex> lock(p->ws_mu);
         if (p->ws && p->ws_device != dev) return BMMC_ERR_INVALID;
         if (!p->ws) {
+            if (debug_fail_alloc()) return BMMC_ERR_OOM;
             if (cudaMalloc(&p->ws, (size_t)array_bytes(p)) != cudaSuccess) {
                 p->ws = nullptr;
                 cudaGetLastError();

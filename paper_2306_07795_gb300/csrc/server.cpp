@@ -12,6 +12,7 @@
 // stream.  The paper has no serving counterpart (Sec. 6 times one array at a
 // time); every request runs the passes of Sec. 5.1 / 5.2 unchanged.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -32,6 +33,7 @@
 #include "bmmc.h"
 #include "bmmc_batch.h"
 #include "bmmc_server.h"
+#include "debug_hooks.hpp"
 
 namespace {
 
@@ -39,6 +41,13 @@ constexpr size_t kAlign = 256;
 constexpr int kMaxStreams = 32;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// An NVTX range for the scope (no cost unless a profiler is attached):
+// submission, admission and retirement show on a profiler's timeline.
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+};
 
 // First-fit allocator over one device block; free ranges kept coalesced.
 class Arena {
@@ -250,6 +259,7 @@ void finish(bmmc_server_s *s, Launch &L)
 // Retire completed launches at the heads of the stream queues.
 bool retire(bmmc_server_s *s)
 {
+    NvtxScope range("bmmc server retire");
     bool any = false;
     for (int i = 0; i < s->nstreams; ++i) {
         auto &q = s->inflight[i];
@@ -374,6 +384,7 @@ bool allocate(bmmc_server_s *s, Req *r)
 // if anything was launched.
 bool admit(bmmc_server_s *s)
 {
+    NvtxScope range("bmmc server admit");
     std::vector<Req *> admitted;
     while (!s->waiting.empty()) {
         Req *r = s->waiting.front();
@@ -574,7 +585,8 @@ int bmmc_server_create(bmmc_server *out, const bmmc_server_config *cfg)
             delete s;
             return BMMC_ERR_CUDA;
         }
-        if (cudaMalloc((void **)&s->arena_mem, cfg->arena_bytes) != cudaSuccess) {
+        if (bmmc::debug_fail_alloc() ||
+            cudaMalloc((void **)&s->arena_mem, cfg->arena_bytes) != cudaSuccess) {
             cudaGetLastError();
             delete s;
             return BMMC_ERR_OOM;
@@ -608,6 +620,7 @@ int bmmc_server_create(bmmc_server *out, const bmmc_server_config *cfg)
 int bmmc_server_submit(bmmc_server s, uint64_t id, int n, const uint64_t *A_rows, uint64_t c,
                        size_t elem_bytes, const void *in)
 {
+    NvtxScope range("bmmc server submit");
     try {
         if (!s || !in) return BMMC_ERR_INVALID;
         if ((uintptr_t)in & 15u) return BMMC_ERR_ALIGN;
