@@ -26,10 +26,14 @@ def to_device(arr):
 
 
 def run_gpu(n, rows, c, e, arr, flags=PAPER, **kw):
+    """The plan's output for arr.  The output buffer starts as all-ones bytes,
+    a value no payload element takes, so a slot the kernel never writes
+    cannot pass for a result left behind by an earlier run."""
     import torch
     p = bm.Plan(n, rows, c, e, flags=flags, **kw)
     x = to_device(arr)
-    y = p(x)
+    y = torch.full_like(x, -1)
+    p(x, out=y)
     torch.cuda.synchronize()
     return y.cpu().numpy().view(np.uint8)
 
@@ -282,7 +286,8 @@ def full_check(n, rows, c, e, flags):
     import torch
     p = bm.Plan(n, rows, c, e, flags=flags)
     x = wl.payload_torch(n, e, seed=7, device="cuda")
-    y = p(x)
+    y = torch.full_like(x, -1)  # all-ones bytes: no payload element is
+    p(x, out=y)                 # all-ones, so a missed write shows
     torch.cuda.synchronize()
     xin = x.cpu().numpy()
     yout = y.cpu().numpy()
