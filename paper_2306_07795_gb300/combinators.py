@@ -34,14 +34,30 @@ def _log2_len(x):
     return n
 
 
+_parm_plans = {}  # (n, mask, element bytes, flags) -> Plan, most recent last
+_PARM_PLANS_MAX = 256
+
+
+def _parm_plan(n, mask, elem_bytes, flags):
+    """The plan of parm's permutation, kept for repeated calls (plans are
+    immutable; the least recently used one is dropped beyond 256)."""
+    key = (n, mask, elem_bytes, flags)
+    plan = _parm_plans.pop(key, None)
+    if plan is None:
+        plan = Plan(n, parm_matrix(n, mask), 0, elem_bytes, flags=flags)
+        if len(_parm_plans) >= _PARM_PLANS_MAX:
+            _parm_plans.pop(next(iter(_parm_plans)))
+    _parm_plans[key] = plan
+    return plan
+
+
 def parm(mask, f, x, flags=B.BMMC_PLAN_PAPER):
     """parm mask f x along the last dimension (differentiable).
 
     f receives a tensor of shape [..., 2, 2^(n-1)] (the two sub-arrays) and
     must return one of the same shape."""
     n = _log2_len(x)
-    rows = parm_matrix(n, mask)
-    plan = Plan(n, rows, 0, x.element_size(), flags=flags)
+    plan = _parm_plan(n, mask, x.element_size(), flags)
     y = bmmc_permute(x, plan)
     half = x.shape[-1] // 2
     z = f(y.reshape(*x.shape[:-1], 2, half))

@@ -65,3 +65,17 @@ def test_pipeline_fuses_adjacent_permutations():
         want = f2.compose(rows, c, want[0], want[1])
     assert (steps[0][1].rows, steps[0][1].c) == tuple(want)
     assert p.num_permutations() == 2
+
+
+def test_parm_plans_are_kept_and_bounded():
+    from paper_2306_07795_gb300 import combinators as cb
+    cb._parm_plans.clear()
+    p1 = cb._parm_plan(8, 0b110, 4, 0)
+    assert cb._parm_plan(8, 0b110, 4, 0) is p1          # reused
+    assert cb._parm_plan(8, 0b110, 8, 0) is not p1      # element size is part of the key
+    assert p1.rows == cb.parm_matrix(8, 0b110)
+    for m in range(1, cb._PARM_PLANS_MAX + 10):
+        cb._parm_plan(10, m, 4, 0)
+    assert len(cb._parm_plans) == cb._PARM_PLANS_MAX
+    assert (8, 0b110, 4, 0) not in cb._parm_plans        # least recently used dropped
+    cb._parm_plans.clear()
