@@ -37,6 +37,8 @@ sys.path.insert(0, ROOT)
 METRIC = ("effective GB/s (2·N·bytes/s) vs GB300 HBM peak & D2D copy; "
           "batched/served p50/p99")
 FALLBACK_HBM_GBS = 6800.0
+# The path copies elements as opaque 4-, 8- and 16-byte blobs.
+DTYPE = "opaque 4/8/16-byte elements"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "bmmc_tiled_pass_traffic.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2306_07795_gb300", "csrc", f)
                   for f in ("kernels.cu", "tile_body.cuh", "pass_desc.h", "plan.cpp")]
@@ -272,37 +274,61 @@ def profiled_traffic(kernel_name):
         return None, None
 
 
+def workload_config(args, world):
+    """The `config` object of both arms' JSON lines (the same workload)."""
+    elems = [int(v) for v in args.elem.split(",")]
+    N = 1 << args.n
+    count = len(elems) * (2 + args.bp + args.tiled + args.dense)
+    return {
+        "workload": "n=%d BMMC permutation set per elem size: bit-reversal, "
+                    "half-swap, %d random BP, %d random tiled-only, %d random "
+                    "dense (random c)" % (args.n, args.bp, args.tiled, args.dense),
+        "n": args.n, "elem_bytes": elems, "strategy": args.strategy,
+        "permutations_per_step": count,
+        "l2": "inputs larger than L2 (%d-%d MiB per array), no flush"
+              % (N * min(elems) >> 20, N * max(elems) >> 20),
+        "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 # ---------------------------------------------------------------------------
 # CPU baseline / reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 
-def oracle_sample(n_sample=24, elems=(4, 8, 16)):
-    """One permutation of each class per element size, at 2^n_sample
-    elements: a bounded sample of the benchmark workload."""
+# Array size (log2 elements) of the oracle's timed sample.
+ORACLE_N = 28
+
+
+def oracle_sample(n, n_dense=4):
+    """The CPU-baseline sample of the n = 28 configuration at 4-byte
+    elements: bit-reversal, half-swap and the first n_dense dense random
+    BMMCs of the benchmark's own set (seeds 1..n_dense, random c)."""
     import workloads as wl
     from oracle import f2
     inv = lambda rows: f2.is_invertible(rows, len(rows))  # noqa: E731
-    items = []
-    for e in elems:
-        k = 8 - {4: 2, 8: 3, 16: 4}[e]
-        items.append(("bit_reverse", e, wl.bit_reverse(n_sample), 0))
-        items.append(("half_swap", e, wl.half_swap(n_sample), 0))
-        items.append(("bp", e, wl.random_bp(n_sample, 1), 0))
-        rows, c = wl.tiled_only_bmmc(n_sample, k, 1, inv)
-        items.append(("tiled_only", e, rows, c))
-        rows, c = wl.dense_bmmc(n_sample, 1, inv)
-        items.append(("dense", e, rows, c))
+    items = [("bit_reverse", 4, wl.bit_reverse(n), 0),
+             ("half_swap", 4, wl.half_swap(n), 0)]
+    for sd in range(1, n_dense + 1):
+        rows, c = wl.dense_bmmc(n, sd, inv)
+        items.append(("dense", 4, rows, c))
     return items
 
 
-def run_oracle_step(n_sample, items, buffers, threads=True):
+def run_oracle_step(n, items, inp, out, threads=True):
+    """Run every permutation of `items` once through the oracle's C loop
+    (into the preallocated `out`); returns the effective bytes 2 N e."""
     import oracle
     moved = 0
     for cls, e, rows, c in items:
-        inp = buffers[e]
-        oracle.apply(n_sample, rows, c, inp, elem_bytes=e, threads=threads)
-        moved += 2 * (1 << n_sample) * e
+        oracle.apply_into(n, rows, c, inp, out, elem_bytes=e, threads=threads)
+        moved += 2 * (1 << n) * e
     return moved
+
+
+def oracle_sample_text():
+    return ("the oracle's C loop out[A x + c] = in[x] (OpenMP over x) on the "
+            "n = %d configuration at 4-byte elements (%d MiB arrays): "
+            "bit-reversal, half-swap and dense random BMMCs seeds 1-4"
+            % (ORACLE_N, (4 << ORACLE_N) >> 20))
 
 
 def cpu_model():
@@ -318,81 +344,81 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(n_sample=24, reps=1):
+def cpu_baseline():
+    """The oracle on the host cores: all cores on the n = 28 sample, one
+    core on part of it, and the n = 20 configuration in full."""
+    import numpy as np
     import oracle
     import workloads as wl
-    items = oracle_sample(n_sample)
-    buffers = {e: wl.payload(n_sample, e) for e in (4, 8, 16)}
-    run_oracle_step(n_sample, items[:1], buffers)  # warm the library
+    n = ORACLE_N
+    items = oracle_sample(n)
+    inp = wl.payload(n, 4)
+    out = np.empty_like(inp)
+    run_oracle_step(n, items[:1], inp, out)  # first touch of both arrays
     t0 = time.perf_counter()
-    moved = 0
-    for _ in range(reps):
-        moved += run_oracle_step(n_sample, items, buffers)
+    moved = run_oracle_step(n, items, inp, out)
     dt = time.perf_counter() - t0
-    out = {"value": moved / dt / 1e9, "unit": "GB/s",
+    res = {"value": round(moved / dt / 1e9, 3), "unit": "GB/s",
            "cores": oracle.num_threads(), "kind": "oracle",
-           "sample": ("C loop out[A x + c] = in[x] (OpenMP over x), 2^%d elements, "
-                      "one bit-reversal, half-swap, random BP, tiled-only and dense "
-                      "BMMC at each of 4, 8, 16 bytes per element; %d pass(es), "
-                      "%.1f s" % (n_sample, reps, dt)),
-           "cpu_model": cpu_model()}
-    # the same classes on one core, at 2^20 elements
-    small = oracle_sample(20)
-    bufs20 = {e: wl.payload(20, e) for e in (4, 8, 16)}
+           "sample": "%s, all cores, %.1f s" % (oracle_sample_text(), dt),
+           "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+    one = items[:2] + items[2:3]
     t0 = time.perf_counter()
-    moved = run_oracle_step(20, small, bufs20, threads=False)
-    out["single_thread"] = {"value": round(moved / (time.perf_counter() - t0) / 1e9, 3),
-                            "unit": "GB/s", "cores": 1,
-                            "sample": "the same 15 permutations at 2^20 elements"}
+    moved = run_oracle_step(n, one, inp, out, threads=False)
+    dt = time.perf_counter() - t0
+    res["single_thread"] = {"value": round(moved / dt / 1e9, 3), "unit": "GB/s", "cores": 1,
+                            "sample": "bit-reversal, half-swap and dense seed 1 of the "
+                                      "same sample on one core, %.1f s" % dt}
+    del inp, out
     # the n = 20 configuration in full: int32 iota, bit-reversal + 16 dense
     from oracle import f2
     inv = lambda rows: f2.is_invertible(rows, len(rows))  # noqa: E731
     c1 = [("bit_reverse", 4, wl.bit_reverse(20), 0)] + \
         [("dense", 4) + tuple(wl.dense_bmmc(20, sd, inv)) for sd in range(1, 17)]
-    import numpy as np
-    iota = {4: np.arange(1 << 20, dtype=np.uint32)}
-    t0 = time.perf_counter()
-    moved = run_oracle_step(20, c1, iota)
-    out["n20_config"] = {"value": round(moved / (time.perf_counter() - t0) / 1e9, 3),
-                         "unit": "GB/s", "cores": oracle.num_threads(),
-                         "sample": "all 17 permutations of the n = 20 configuration"}
-    return out
+    iota = np.arange(1 << 20, dtype=np.uint32)
+    out20 = np.empty_like(iota)
+    for threads, key in ((True, "n20_config"), (False, "n20_config_single_thread")):
+        t0 = time.perf_counter()
+        moved = run_oracle_step(20, c1, iota, out20, threads=threads)
+        res[key] = {"value": round(moved / (time.perf_counter() - t0) / 1e9, 3),
+                    "unit": "GB/s", "cores": oracle.num_threads() if threads else 1,
+                    "sample": "all 17 permutations of the n = 20 configuration"}
+    return res
 
 
 def reference_arm(args):
+    """The oracle, as it stands, on the host cores: each step runs the
+    n = 28 sample once on all cores (rank 0 only)."""
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
+    import numpy as np
     import oracle
     import workloads as wl
-    n_sample = 24
-    items = oracle_sample(n_sample)
-    buffers = {e: wl.payload(n_sample, e) for e in (4, 8, 16)}
+    n = ORACLE_N
+    items = oracle_sample(n)
+    inp = wl.payload(n, 4)
+    out = np.empty_like(inp)
     for _ in range(args.warmup):
-        run_oracle_step(n_sample, items, buffers)
+        run_oracle_step(n, items, inp, out)
     t0 = time.perf_counter()
     moved = 0
     for _ in range(args.steps):
-        moved += run_oracle_step(n_sample, items, buffers)
+        moved += run_oracle_step(n, items, inp, out)
     dt = time.perf_counter() - t0
     value = moved / dt / 1e9
+    sample = "%s, all cores, per step" % oracle_sample_text()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
         "data": "synthetic",
-        "config": {"workload": "n=28 BMMC permutation set per elem size: bit-reversal, "
-                               "half-swap, %d random BP, %d random tiled-only, %d random "
-                               "dense (random c)" % (args.bp, args.tiled, args.dense),
-                   "n": args.n, "elem_bytes": [int(v) for v in args.elem.split(",")],
-                   "strategy": args.strategy,
-                   "reference_sample": "each step: one permutation of each class per "
-                                       "element size at 2^%d elements" % n_sample},
+        "config": workload_config(args, args.gpus),
         "cpu_baseline": {"value": value, "unit": "GB/s",
                          "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": "2^24 elements, one permutation of each class "
-                                   "per element size, per step"},
+                         "sample": sample, "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -1008,24 +1034,16 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(reps=20)
+        cpu = cpu_baseline()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s",
             "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": round(elapsed_ms / K, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
             "data": "synthetic",
-            "config": {
-                "workload": "n=28 BMMC permutation set per elem size: bit-reversal, "
-                            "half-swap, %d random BP, %d random tiled-only, %d random "
-                            "dense (random c)" % (args.bp, args.tiled, args.dense),
-                "n": n, "elem_bytes": elems, "strategy": args.strategy,
-                "permutations_per_step": len(items),
-                "l2": "inputs larger than L2 (%d-%d MiB per array), no flush"
-                      % (N * min(elems) >> 20, N * max(elems) >> 20),
-                "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(args, world),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -147,6 +147,15 @@ int bmmc_plan_inverse(bmmc_plan p, bmmc_plan *out);
  * Errors: INVALID (NULL or mismatched plans), OOM. */
 int bmmc_plan_compose(bmmc_plan second, bmmc_plan first, bmmc_plan *out);
 
+/* The same permutation applied to each of 2^b arrays stored one after
+ * another: the plan of diag(A, I_b) on n + b index bits with complement c.
+ * The low n bits of an index pick an element of one array and the high b
+ * bits the array, which keeps its place (Sec. 3: the high output bits equal
+ * the high input bits).  The new plan takes p's element size and options.
+ * Host only.
+ * Errors: INVALID (NULL plan or out, b < 0, n + b > 32), OOM. */
+int bmmc_plan_lift(bmmc_plan p, int b, bmmc_plan *out);
+
 /* The matrix A of the parm combinator (Sec. 6.2), for which
  *     parm mask f = bmmc(A^{-1}, 0) o parm 2^{n-1} f o bmmc(A, 0):
  * y_i = x_i for i < lsb(mask), y_i = x_{i+1} for lsb(mask) <= i < n - 1, and
@@ -219,20 +228,46 @@ int bmmc_execute_host(bmmc_plan p, const void *host_in, void *host_out, void *de
  * needs no intermediate array and runs exactly as with bmmc_execute_ws.
  *
  * in, out, stream: as for bmmc_execute.
- * The first call on a device looks up the array's device address (a one-time
- * set-up per device, done with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array and
- * leaves its contents behind: nothing in it needs clearing, because the first
- * pass overwrites all bytes the second pass reads, but two calls whose
- * executions overlap on the GPU (different streams, not ordered by events)
- * race on it and give wrong results.  Order such calls.
- * Errors: INVALID, ALIAS, ALIGN, CUDA, and TOO_LARGE when the plan's
- * workspace (2^n * elem_bytes) exceeds BMMC_STATIC_SCRATCH_BYTES; no device
- * memory is allocated or freed in any case.
+ * Each call looks up the array's device address in the current context
+ * (the address changes after cudaDeviceReset or under another context).
+ * With CUDA's lazy module loading, the default, the library's device code,
+ * and so the array, is loaded on a device by the first call there: that
+ * call can fail with OOM when the device has no room left for it.  While the
+ * stream is being captured into a CUDA graph, the call takes the address of
+ * the last lookup on the device instead; make a call on the device before
+ * any stream capture (otherwise INVALID).  Every call on a device shares the
+ * one array and leaves its contents behind: nothing in it needs clearing,
+ * because the first pass overwrites all bytes the second pass reads, but two
+ * calls whose executions overlap on the GPU (different streams, not ordered
+ * by events) race on it and give wrong results.  Order such calls.
+ * Errors: INVALID, ALIAS, ALIGN, CUDA, OOM (the array could not be loaded),
+ * UNSUPPORTED (device index 64 or above), and TOO_LARGE when the plan's
+ * workspace (2^n * elem_bytes) exceeds BMMC_STATIC_SCRATCH_BYTES.  The call
+ * itself never allocates or frees device memory.
  */
 #define BMMC_STATIC_SCRATCH_BYTES (32u << 20)
 int bmmc_execute_static_ws(bmmc_plan p, const void *in, void *out,
                            bmmc_stream_t stream);
+
+/*
+ * The sorting network of Sec. 6.1 (even/odd merge sort with a balanced
+ * periodic merger, written with parm) unrolled into n (n + 1) / 2 stages:
+ * stage s permutes the array of 2^n keys by the matrix M_s and then orders
+ * every pair (2j, 2j + 1) (a column of comparators, see bmmc_execute_ce);
+ * after the last stage the array is permuted by the final matrix.  Each M_s
+ * is the product, by the fusion rule of Sec. 3, of the parm permutations
+ * (Sec. 6.2) between two comparator columns.  Host only.
+ *
+ * stage_rows  NULL, or room for max_stages * n row masks: stage s's matrix
+ *             is written at stage_rows[s * n .. s * n + n - 1].
+ * final_rows  NULL, or room for n row masks.
+ * final_is_identity  NULL, or set to 1 when the final matrix is the identity
+ *             (so no final permutation is needed), else 0.
+ * Returns the number of stages, n (n + 1) / 2, or a negative code.
+ * Errors: INVALID (n outside 1..30, max_stages too small), OOM.
+ */
+int bmmc_sort_schedule(int n, uint64_t *stage_rows, int max_stages,
+                       uint64_t *final_rows, int *final_is_identity);
 
 /* Key types for bmmc_execute_ce: how the bytes of an element compare. */
 enum bmmc_key_type {

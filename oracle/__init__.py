@@ -101,6 +101,17 @@ def apply(n, rows, c, arr, elem_bytes=None, threads=True):
     return out
 
 
+def apply_into(n, rows, c, arr, out, elem_bytes=None, threads=True):
+    """As ``apply``, writing into the preallocated contiguous buffer ``out``
+    (the same size as ``arr``), so that a timed loop allocates nothing."""
+    e = elem_bytes or (arr.nbytes >> n)
+    _check_buf(arr, n, e)
+    _check_buf(out, n, e)
+    fn = _load().bmmc_ref_apply_mt if threads else _load().bmmc_ref_apply
+    fn(n, _rows_arg(rows), c, e, arr.ctypes.data, out.ctypes.data)
+    return out
+
+
 def grad(n, rows, c, gy, elem_bytes=None):
     """gx[x] = gy[A x + c]: the gradient of the forward permutation."""
     e = elem_bytes or (gy.nbytes >> n)

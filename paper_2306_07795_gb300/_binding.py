@@ -34,6 +34,7 @@ EXPORTED = (
     "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws", "bmmc_execute_host",
     "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
     "bmmc_strerror", "bmmc_plan_compose", "bmmc_parm_matrix", "bmmc_execute_ce",
+    "bmmc_plan_lift", "bmmc_sort_schedule",
     # include/bmmc_batch.h
     "bmmc_batch_workspace_bytes", "bmmc_batch_table_bytes", "bmmc_batch_create",
     "bmmc_batch_execute",
@@ -119,6 +120,9 @@ def lib():
         "bmmc_plan_compose": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
         "bmmc_execute_ce": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, vp]),
         "bmmc_parm_matrix": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, u64p]),
+        "bmmc_plan_lift": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp)]),
+        "bmmc_sort_schedule": (ctypes.c_int, [ctypes.c_int, u64p, ctypes.c_int, u64p,
+                                              ctypes.POINTER(ctypes.c_int)]),
         "bmmc_batch_workspace_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_table_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), vpp, ctypes.c_int,
@@ -270,6 +274,26 @@ BMMC_KEY_I64, BMMC_KEY_U64, BMMC_KEY_F64 = 4, 5, 6
 def bmmc_execute_ce(h, in_ptr, out_ptr, ws_ptr, key_type, stream=0):
     _check(lib().bmmc_execute_ce(h, in_ptr, out_ptr, ws_ptr, key_type, stream),
            "bmmc_execute_ce")
+
+
+def bmmc_plan_lift(h, b):
+    out = ctypes.c_void_p()
+    _check(lib().bmmc_plan_lift(h, b, ctypes.byref(out)), "bmmc_plan_lift")
+    return out
+
+
+def bmmc_sort_schedule(n):
+    """(stage matrices, final matrix, final is the identity) of the sorting
+    network of 2^n keys."""
+    count = lib().bmmc_sort_schedule(n, None, 0, None, None)
+    _check(min(count, 0), "bmmc_sort_schedule")
+    flat = (ctypes.c_uint64 * (count * n))()
+    fin = (ctypes.c_uint64 * n)()
+    ident = ctypes.c_int()
+    got = lib().bmmc_sort_schedule(n, flat, count, fin, ctypes.byref(ident))
+    _check(min(got, 0), "bmmc_sort_schedule")
+    stages = [[int(r) for r in flat[s * n:(s + 1) * n]] for s in range(count)]
+    return stages, [int(r) for r in fin], bool(ident.value)
 
 
 def bmmc_parm_matrix(n, mask):

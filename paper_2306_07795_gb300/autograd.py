@@ -26,10 +26,7 @@ def _lifted_plan(plan, rows_total):
     hit = _lift_cache.get(key)
     if hit is not None and hit[0] is plan:
         return hit[1]
-    n = plan.n
-    rows = list(plan.rows) + [1 << (n + j) for j in range(b)]
-    lifted = Plan(n + b, rows, plan.c, plan.elem_bytes, plan.flags,
-                  plan.seg_bits, plan.cta_tile_log2)
+    lifted = plan.lift(b)
     _lift_cache[key] = (plan, lifted)
     return lifted
 

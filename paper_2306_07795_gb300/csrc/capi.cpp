@@ -231,6 +231,27 @@ int bmmc_plan_compose(bmmc_plan second, bmmc_plan first, bmmc_plan *out)
     });
 }
 
+int bmmc_plan_lift(bmmc_plan p, int b, bmmc_plan *out)
+{
+    if (!out) return BMMC_ERR_INVALID;
+    *out = nullptr;
+    if (!p || b < 0 || p->n + b > kMaxN) return BMMC_ERR_INVALID;
+    // diag(A, I_b): the low n output bits are A x_low + c, the high b bits
+    // are copied (each array keeps its place)
+    uint64_t rows[64];
+    for (int i = 0; i < p->n; ++i) rows[i] = p->a.r[i];
+    for (int i = p->n; i < p->n + b; ++i) rows[i] = 1ull << i;
+    bmmc_plan_options o;
+    memset(&o, 0, sizeof(o));
+    o.flags = p->opt.flags;
+    o.seg_bits = p->opt.seg_bits;
+    o.cta_tile_log2 = p->opt.cta_tile_log2;
+    o.tile_order = p->opt.tile_order;
+    return guarded([&] {
+        return create_impl(out, p->n + b, rows, p->c, (size_t)1 << p->e_log, &o);
+    });
+}
+
 int bmmc_parm_matrix(int n, uint64_t mask, uint64_t *rows_out)
 {
     if (n < 1 || n > kMaxN || !rows_out) return BMMC_ERR_INVALID;

@@ -81,6 +81,16 @@ class Plan:
                                  self.tile_order, _handle=h)
         return self._inverse
 
+    def lift(self, b):
+        """Plan of the same permutation on each of 2^b arrays stored one after
+        another (diag(A, I_b), bmmc_plan_lift)."""
+        if b == 0:
+            return self
+        h = B.bmmc_plan_lift(self._h, b)
+        rows, c = B.bmmc_plan_matrix(h, self.n + b)
+        return Plan(self.n + b, rows, c, self.elem_bytes, self.flags, self.seg_bits,
+                    self.cta_tile_log2, self.tile_order, _handle=h)
+
     # -- execution ----------------------------------------------------------
     def _check_tensor(self, t, name):
         if not t.is_cuda:

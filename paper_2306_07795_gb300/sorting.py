@@ -21,8 +21,8 @@ library (bmmc_execute_ce: the comparator runs in registers before the
 permutation's 16-byte store), and the whole network is a CUDA-graph-friendly
 sequence of single-pass launches.
 
-Host-side planning uses small F2 matrix products over row masks; the data
-path is entirely library kernels.
+The schedule comes from the library (bmmc_sort_schedule) and the lifted
+plans from bmmc_plan_lift; the data path is entirely library kernels.
 """
 
 from . import _binding as B
@@ -45,71 +45,11 @@ def _key_for(dtype):
     return _KEYS[dtype]
 
 
-# ---- host planning: programs of ("perm", rows) and ("ce",) over m bits -----
-
-def _mul(a, b):
-    """(a b) x = a (b x) over F2, matrices as row masks."""
-    out = []
-    for row in a:
-        acc = 0
-        j = 0
-        while row:
-            if row & 1:
-                acc ^= b[j]
-            row >>= 1
-            j += 1
-        out.append(acc)
-    return out
-
-
-def _identity(m):
-    return [1 << i for i in range(m)]
-
-
-def _inverse(rows):
-    m = len(rows)
-    p = Plan(m, rows, 0, 4, flags=B.BMMC_PLAN_SINGLE_PASS)
-    return B.bmmc_plan_matrix(B.bmmc_plan_inverse(p.handle), m)[0]
-
-
-def _lift(prog, m):
-    """A program on the low m bits, acting on m + 1 bits (top bit kept)."""
-    return [("perm", op[1] + [1 << m]) if op[0] == "perm" else op for op in prog]
-
-
-def _parm(mask, inner, n):
-    a = B.bmmc_parm_matrix(n, mask)
-    return [("perm", a)] + _lift(inner, n - 1) + [("perm", _inverse(a))]
-
-
-def _vcolumn(n):
-    return [("ce",)] if n == 1 else _parm(3, _vcolumn(n - 1), n)
-
-
-def _merge(n):
-    if n == 0:
-        return []
-    return _vcolumn(n) + _parm(1 << (n - 1), _merge(n - 1), n)
-
-
-def _sort(n):
-    if n == 0:
-        return []
-    return _parm(1, _sort(n - 1), n) + _merge(n)
-
-
 def schedule(n):
-    """The fused program of sort n: (stage matrices, final matrix).  Stage s
-    is 'permute by M_s, then order adjacent pairs'."""
-    stages = []
-    acc = _identity(n)
-    for op in _sort(n):
-        if op[0] == "perm":
-            acc = _mul(op[1], acc)
-        else:
-            stages.append(acc)
-            acc = _identity(n)
-    return stages, acc
+    """The fused program of sort n from the library (bmmc_sort_schedule):
+    (stage matrices, final matrix, final is the identity).  Stage s is
+    'permute by M_s, then order adjacent pairs'."""
+    return B.bmmc_sort_schedule(n)
 
 
 class SortingNetwork:
@@ -121,7 +61,7 @@ class SortingNetwork:
         if n < 1 or n > 30:
             raise ValueError("n must be in 1..30")
         self.n = n
-        self.stage_rows, self.final_rows = schedule(n)
+        self.stage_rows, self.final_rows, self._final_identity = schedule(n)
         self._plans = {}
 
     @property
@@ -131,11 +71,11 @@ class SortingNetwork:
     def _plans_for(self, elem_bytes, b):
         key = (elem_bytes, b)
         if key not in self._plans:
-            lift = [1 << (self.n + j) for j in range(b)]
-            mk = lambda rows: Plan(self.n + b, rows + lift, 0, elem_bytes,  # noqa: E731
-                                   flags=B.BMMC_PLAN_SINGLE_PASS)
+            def mk(rows):
+                return Plan(self.n, rows, 0, elem_bytes,
+                            flags=B.BMMC_PLAN_SINGLE_PASS).lift(b)
             stages = [mk(r) for r in self.stage_rows]
-            final = None if self.final_rows == _identity(self.n) else mk(self.final_rows)
+            final = None if self._final_identity else mk(self.final_rows)
             self._plans[key] = (stages, final)
         return self._plans[key]
 

@@ -312,7 +312,7 @@ def test_n28_full_size(e):
 
 def sampled_check(n, rows, c, flags, samples=1 << 20):
     """n up to 32 with 4-byte iota payload: out[A x + c] must equal x, for a
-    random sample of x (destinations from the oracle's numpy definition)."""
+    random sample of x (destinations from the oracle's index_of)."""
     import torch
     p = bm.Plan(n, rows, c, 4, flags=flags)
     x = torch.arange(1 << n, dtype=torch.int64, device="cuda").to(torch.int32)
@@ -322,14 +322,7 @@ def sampled_check(n, rows, c, flags, samples=1 << 20):
     g = wl.rng(n)
     xs = g.integers(0, 1 << n, size=samples, dtype=np.uint64)
     xs[:2] = [0, (1 << n) - 1]
-    ys = np.zeros_like(xs)
-    for i, row in enumerate(rows):
-        masked = xs & np.uint64(row)
-        par = np.zeros_like(masked)
-        for b in range(n):
-            par ^= (masked >> np.uint64(b)) & np.uint64(1)
-        ys |= par << np.uint64(i)
-    ys ^= np.uint64(c)
+    ys = f2.index_of(rows, c, xs)
     got = y[torch.from_numpy(ys.astype(np.int64)).cuda()].cpu().numpy()
     assert np.array_equal(got.view(np.uint32), xs.astype(np.uint32))
 

@@ -67,3 +67,24 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = bench.parse_args()
     assert bench.reference_arm(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_reports_our_config(monkeypatch, capsys):
+    """The reference arm times the oracle on the same workload config as our
+    arm's line (here on a small sample size, to keep the test short)."""
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "ORACLE_N", 12)
+    import sys
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2",
+                                      "--warmup", "1"])
+    args = bench.parse_args()
+    assert bench.reference_arm(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["config"] == bench.workload_config(args, 1)
+    assert line["cpu_baseline"]["value"] == line["value"] > 0
+    assert "n = 12" in line["cpu_baseline"]["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0

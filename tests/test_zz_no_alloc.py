@@ -5,8 +5,10 @@ all of it, a latency-critical loop where cudaMalloc could stall, a program
 with a fixed memory budget) run two-pass plans through this entry point,
 which keeps the intermediate array in a static device array instead of
 allocating one.  These tests call it through the C ABI and require results
-identical, byte for byte, to bmmc_execute_ws with a caller workspace, on two
-calls in a row (the second call reuses the array the first one left behind).
+identical, byte for byte, to bmmc_execute_ws with a caller workspace and to
+the CPU oracle, on two calls in a row (the second call reuses the array the
+first one left behind), and check that a call leaves the device's free memory
+unchanged.
 
 The file is named to be collected last, so that a run stopping at the first
 failure has run every other test before it.
@@ -17,6 +19,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from oracle import f2
 import paper_2306_07795_gb300 as bm
 import workloads as wl
@@ -78,6 +81,35 @@ def test_static_scratch_matches_workspace_entry_point(n, e):
     got_again = _static(plans[0], xs[0])
     torch.cuda.synchronize()
     assert torch.equal(got_again, want[0])
+    # both results against the CPU oracle's out[A x + c] = in[x]
+    for p, x, got in ((plans[0], xs[0], got_again), (plans[1], xs[1], got_second)):
+        bad = oracle.count_mismatch(n, p.rows, p.c, x.cpu().numpy(), got.cpu().numpy(),
+                                    elem_bytes=e)
+        assert bad == 0, bad
+
+
+def test_static_scratch_allocates_nothing():
+    """After a first call (which may load the library's device code), a
+    two-pass call leaves the device's free memory exactly as it was."""
+    import torch
+    n, e = 20, 4
+    rows, c = wl.dense_bmmc(n, 13, _inv)
+    p = bm.Plan(n, rows, c, e)
+    assert p.num_passes == 2
+    x = _device_payload(n, e, seed=5)
+    _static(p, x)
+    torch.cuda.synchronize()
+    out = torch.full_like(x, -1)
+    free_before = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        rc = bm.lib().bmmc_execute_static_ws(
+            p.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == bm.BMMC_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    bad = oracle.count_mismatch(n, rows, c, x.cpu().numpy(), out.cpu().numpy(), elem_bytes=e)
+    assert bad == 0
 
 
 def test_static_scratch_one_pass_plan_needs_no_scratch():
