@@ -651,26 +651,31 @@ def bench_n20(dev, reps=50):
 
 
 def bench_sorting(dev):
-    """The Sec. 6.1 sorting network (n(n+1)/2 fused permute-and-compare
-    passes) on float32 keys, beside torch.sort of the same keys."""
+    """The Sec. 6.1 sorting network on float32 keys: fused passes (many
+    comparator stages per pass, include/bmmc_sort.h) and one
+    permute-and-compare pass per stage, beside torch.sort of the same keys."""
     import torch
     from paper_2306_07795_gb300.sorting import SortingNetwork
     out = {}
     for n in (20, 24):
         x = torch.randn(1 << n, device=dev)
-        net = SortingNetwork(n)
-        ms = _time_ms(lambda: net(x), dev, 5)
-        graph, gout = net.capture(x)
-        gms = _time_ms(graph.replay, dev, 10)
+        want = torch.sort(x).values
         ref = _time_ms(lambda: torch.sort(x), dev, 5)
-        passes = net.num_stages + 1
-        out["n%d" % n] = {"passes": passes, "ms": round(ms, 3), "graph_ms": round(gms, 3),
-                          "torch_sort_ms": round(ref, 3),
-                          "pass_gbs": round(passes * 2 * x.numel() * 4 / (gms / 1e3) / 1e9, 1)}
-        graph.replay()
-        torch.cuda.synchronize(dev)
-        assert torch.equal(gout, torch.sort(x).values)
-        del graph
+        res = {"stages": n * (n + 1) // 2, "torch_sort_ms": round(ref, 3)}
+        for name, net in (("fused", SortingNetwork(n)),
+                          ("stagewise", SortingNetwork(n, fused=False))):
+            ms = _time_ms(lambda: net(x), dev, 5)
+            graph, gout = net.capture(x)
+            gms = _time_ms(graph.replay, dev, 10)
+            passes = net.num_passes(torch.float32)
+            res[name] = {"passes": passes, "ms": round(ms, 3), "graph_ms": round(gms, 3),
+                         "pass_gbs": round(passes * 2 * x.numel() * 4 / (gms / 1e3) / 1e9, 1),
+                         "vs_torch_sort": round(ref / gms, 3)}
+            graph.replay()
+            torch.cuda.synchronize(dev)
+            assert torch.equal(gout, want)
+            del graph, gout
+        out["n%d" % n] = res
     return out
 
 

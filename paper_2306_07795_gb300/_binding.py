@@ -35,6 +35,10 @@ EXPORTED = (
     "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
     "bmmc_strerror", "bmmc_plan_compose", "bmmc_parm_matrix", "bmmc_execute_ce",
     "bmmc_plan_lift", "bmmc_sort_schedule",
+    # include/bmmc_sort.h
+    "bmmc_sort_plan_create", "bmmc_sort_plan_destroy", "bmmc_sort_plan_num_passes",
+    "bmmc_sort_workspace_bytes", "bmmc_sort_execute", "bmmc_sort_plan_emulate",
+    "bmmc_sort_plan_describe",
     # include/bmmc_batch.h
     "bmmc_batch_workspace_bytes", "bmmc_batch_table_bytes", "bmmc_batch_create",
     "bmmc_batch_execute",
@@ -71,6 +75,10 @@ class BmmcError(RuntimeError):
         self.code = code
         msg = lib().bmmc_strerror(code).decode()
         super().__init__("%s failed: %s (%d)" % (what, msg, code))
+
+
+class bmmc_sort_options(ctypes.Structure):
+    _fields_ = [("block_log2", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class bmmc_plan_options(ctypes.Structure):
@@ -123,6 +131,15 @@ def lib():
         "bmmc_plan_lift": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp)]),
         "bmmc_sort_schedule": (ctypes.c_int, [ctypes.c_int, u64p, ctypes.c_int, u64p,
                                               ctypes.POINTER(ctypes.c_int)]),
+        "bmmc_sort_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(bmmc_sort_options)]),
+        "bmmc_sort_plan_destroy": (None, [vp]),
+        "bmmc_sort_plan_num_passes": (ctypes.c_int, [vp]),
+        "bmmc_sort_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "bmmc_sort_execute": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bmmc_sort_plan_emulate": (ctypes.c_int, [vp, vp, vp]),
+        "bmmc_sort_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "bmmc_batch_workspace_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_table_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), vpp, ctypes.c_int,
@@ -300,6 +317,45 @@ def bmmc_parm_matrix(n, mask):
     rows = (ctypes.c_uint64 * n)()
     _check(lib().bmmc_parm_matrix(n, mask, rows), "bmmc_parm_matrix")
     return [int(r) for r in rows]
+
+
+# ---------------------------------------------------------------------------
+# include/bmmc_sort.h
+# ---------------------------------------------------------------------------
+
+def bmmc_sort_plan_create(n, b, key_type, block_log2=0):
+    h = ctypes.c_void_p()
+    o = bmmc_sort_options(block_log2)
+    _check(lib().bmmc_sort_plan_create(ctypes.byref(h), n, b, key_type, ctypes.byref(o)),
+           "bmmc_sort_plan_create")
+    return h
+
+
+def bmmc_sort_plan_destroy(h):
+    lib().bmmc_sort_plan_destroy(h)
+
+
+def bmmc_sort_plan_num_passes(h):
+    return lib().bmmc_sort_plan_num_passes(h)
+
+
+def bmmc_sort_workspace_bytes(h):
+    return int(lib().bmmc_sort_workspace_bytes(h))
+
+
+def bmmc_sort_execute(h, in_ptr, out_ptr, ws_ptr, stream=0):
+    _check(lib().bmmc_sort_execute(h, in_ptr, out_ptr, ws_ptr, stream), "bmmc_sort_execute")
+
+
+def bmmc_sort_plan_emulate(h, in_ptr, out_ptr):
+    _check(lib().bmmc_sort_plan_emulate(h, in_ptr, out_ptr), "bmmc_sort_plan_emulate")
+
+
+def bmmc_sort_plan_describe(h):
+    need = lib().bmmc_sort_plan_describe(h, None, 0)
+    buf = ctypes.create_string_buffer(need + 1)
+    lib().bmmc_sort_plan_describe(h, buf, need + 1)
+    return json.loads(buf.value.decode())
 
 
 # ---------------------------------------------------------------------------

@@ -105,6 +105,13 @@ int wavefronts(const uint32_t *delta_words, int group_bits)
 int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
                 const PlanOptions &opt, PassDesc *desc, PassInfo *info)
 {
+    return derive_pass_span(t, c, n, e_log, opt, nullptr, 0, desc, info, nullptr);
+}
+
+int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
+                     const PlanOptions &opt, const uint64_t *span, int span_count,
+                     PassDesc *desc, PassInfo *info, SlotMap *map)
+{
     PassDesc &d = *desc;
     memset(&d, 0, sizeof(d));
     *info = PassInfo();
@@ -215,7 +222,7 @@ int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
     // order (2): alternate the next input-adjacent bit with the next bit whose
     // image moves the output by the smallest power of two, so that blocks
     // running at the same time are local in the output as well.
-    if (opt.tile_order == 2 && ntb > 1) {
+    if (opt.tile_order == 2 && ntb > 1 && !span) {
         int outpos[64];
         for (int j = 0; j < ntb; ++j) {
             const uint64_t h = t.col(wb[j]) & ~lowmask;
@@ -243,11 +250,53 @@ int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
     info->n_over = k - m;
     info->tiled = (f2::tiled_columns(t, k) != 0) ? 1 : 0;
 
+    // Tile-index vectors: by default the unit vectors of the tile bits (the
+    // first `it` of them index the tiles inside a thread block).  With a
+    // prescribed block span, the block's tiles are indexed by a basis of
+    // span + V modulo V instead, and the thread blocks by the unit vectors of
+    // the tile bits that complete it.  Every vector is reduced to zero low
+    // bits and zero pivot bits (the same coset of V), so that tile bases never
+    // have a component inside V.
+    uint64_t tvec[64];
+    int it_span = -1;
+    if (span) {
+        auto reduce = [&](uint64_t x) {
+            x &= ~lowmask;
+            for (int j = 0; j < m; ++j)
+                if ((x >> piv[j]) & 1ull) x ^= rowv[j];
+            return x;
+        };
+        uint64_t ech[64];  // echelon copy for independence tests (pivot = top bit)
+        int ne = 0;
+        auto insert = [&](uint64_t x) {
+            uint64_t y = x;
+            for (int i = 0; i < ne; ++i)
+                if ((y >> (63 - __builtin_clzll(ech[i]))) & 1ull) y ^= ech[i];
+            if (!y) return false;
+            ech[ne++] = y;
+            for (int i = ne - 1; i > 0 && ech[i] > ech[i - 1]; --i) {
+                uint64_t tmp = ech[i]; ech[i] = ech[i - 1]; ech[i - 1] = tmp;
+            }
+            return true;
+        };
+        int cnt = 0;
+        for (int i = 0; i < span_count; ++i) {
+            const uint64_t x = reduce(span[i]);
+            if (x && insert(x)) tvec[cnt++] = x;
+        }
+        it_span = cnt;
+        for (int j = 0; j < ntb; ++j)
+            if (insert(1ull << wb[j])) tvec[cnt++] = 1ull << wb[j];
+        if (cnt != ntb) return -3;
+    } else {
+        for (int j = 0; j < ntb; ++j) tvec[j] = 1ull << wb[j];
+    }
+
     // Per-tile-bit contributions.
     uint32_t tin[64], tout[64], tsrc[64];
     for (int j = 0; j < ntb; ++j) {
-        uint64_t col = t.col(wb[j]);
-        tin[j] = (uint32_t)(1ull << wb[j]);
+        uint64_t col = t.apply(tvec[j]);
+        tin[j] = (uint32_t)tvec[j];
         tout[j] = (uint32_t)(col & ~lowmask);
         tsrc[j] = Phi(B(col & lowmask));
     }
@@ -260,6 +309,7 @@ int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
     int it = target - (k + m + e_log);
     if (it < 0) it = 0;
     if (it > ntb) it = ntb;
+    if (span) it = it_span;
     const int P = k + m + it;       // elements per block = 2^P
     const int C = P - w_log;        // chunks per block = 2^C
     if (P + e_log > 17) return -3;  // 128 KiB of shared memory at most
@@ -460,6 +510,14 @@ int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
         for (int b = 0; b < 5; ++b) dw[b] = sw(ic_p[b]) >> w_log;  // 16-byte words
         info->wavefronts_load = wavefronts(dw, 3);
         info->ideal_load = 4;
+    }
+    if (map) {
+        map->P = P;
+        map->w_log = w_log;
+        for (int q = 0; q < 3; ++q) map->sigma[q] = sw.sigma[q];
+        for (int i = 0; i < k; ++i) map->lam[i] = 1u << i;
+        for (int j = 0; j < m; ++j) map->lam[k + j] = (uint32_t)rowv[j];
+        for (int j = 0; j < it; ++j) map->lam[k + m + j] = tin[j];
     }
     info->wavefronts_store = best_wf;
     info->ideal_store = ideal_store;

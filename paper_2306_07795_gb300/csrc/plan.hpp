@@ -34,6 +34,34 @@ struct PassInfo {
 int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
                 const PlanOptions &opt, PassDesc *desc, PassInfo *info);
 
+// How the shared-memory slots of a thread block map to input positions:
+// slot s (element units, before the swizzle) of the block whose input base
+// is x_b holds input element x_b + sum of lam[i] over the set bits i of s.
+// The physical slot of s is swz(s): s with bit w_log + q flipped by the
+// parity of (s & sigma[q]), q < 3 (an involution).
+struct SlotMap {
+    int P = 0;        // slot bits: a block holds 2^P elements
+    int w_log = 0;    // elements per 16-byte chunk = 2^w_log
+    uint32_t sigma[3] = {0, 0, 0};
+    uint32_t lam[32] = {};
+
+    uint32_t swz(uint32_t s) const
+    {
+        uint32_t x = s;
+        for (int q = 0; q < 3; ++q)
+            x ^= (uint32_t)__builtin_parity(s & sigma[q]) << (w_log + q);
+        return x;
+    }
+};
+
+// As derive_pass, with the thread block's span of input positions forced to
+// contain span[0..span_count) (plus the tile subspace V); the block then holds
+// 2^(k + m + it) elements with `it` set by the span, and the other index bits
+// become thread-block bits.  map (may be NULL) receives the slot map.
+int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
+                     const PlanOptions &opt, const uint64_t *span, int span_count,
+                     PassDesc *desc, PassInfo *info, SlotMap *map);
+
 // Walk the tables of a pass on the host (see bmmc_plan_verify).  Returns 0 if
 // every check passes.
 int verify_pass(const PassDesc &d, const f2::Mat &t, uint64_t c,

@@ -52,21 +52,70 @@ def schedule(n):
     return B.bmmc_sort_schedule(n)
 
 
+class _SortPlan:
+    """Owner of one bmmc_sort_plan handle (fused passes)."""
+
+    def __init__(self, n, b, key, block_log2):
+        self.h = B.bmmc_sort_plan_create(n, b, key, block_log2)
+        self.ws_bytes = B.bmmc_sort_workspace_bytes(self.h)
+        self.passes = B.bmmc_sort_plan_num_passes(self.h)
+
+    def describe(self):
+        return B.bmmc_sort_plan_describe(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None:
+            try:
+                B.bmmc_sort_plan_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+
 class SortingNetwork:
     """Sorts the last dimension (2^n elements) of int32 / float32 / int64 /
     float64 tensors with the network of Sec. 6.1; leading dimensions holding
-    2^b rows are sorted independently in the same passes."""
+    2^b rows are sorted independently in the same passes.
 
-    def __init__(self, n):
+    fused=True (default) runs the network through a sort plan
+    (include/bmmc_sort.h): many comparator stages per pass, on tiles held in
+    shared memory and registers.  fused=False runs one permute-and-compare
+    pass per stage (bmmc_execute_ce), the straightforward form of Sec. 6.1's
+    program; both give the same output bit for bit."""
+
+    def __init__(self, n, fused=True, block_log2=0):
         if n < 1 or n > 30:
             raise ValueError("n must be in 1..30")
         self.n = n
+        self.fused = fused
+        self.block_log2 = block_log2
         self.stage_rows, self.final_rows, self._final_identity = schedule(n)
         self._plans = {}
 
     @property
     def num_stages(self):
         return len(self.stage_rows)
+
+    def num_passes(self, dtype, rows=1):
+        """Kernel launches one call makes for `rows` rows of `dtype` keys."""
+        import torch
+        elem_bytes, key = _key_for(dtype)
+        b = rows.bit_length() - 1
+        if self.fused:
+            return self._sort_plan(key, b).passes
+        stages, final = self._plans_for(elem_bytes, b)
+        return len(stages) + (final is not None)
+
+    def _sort_plan(self, key, b):
+        k = ("fused", key, b)
+        if k not in self._plans:
+            self._plans[k] = _SortPlan(self.n, b, key, self.block_log2)
+        return self._plans[k]
+
+    def describe(self, dtype, rows=1):
+        _, key = _key_for(dtype)
+        return self._sort_plan(key, rows.bit_length() - 1).describe()
 
     def _plans_for(self, elem_bytes, b):
         key = (elem_bytes, b)
@@ -95,16 +144,28 @@ class SortingNetwork:
     def __call__(self, x, stream=None):
         import torch
         elem_bytes, key = _key_for(x.dtype)
+        if not x.is_cuda:
+            raise ValueError("x must be a CUDA tensor (there is no CPU path)")
         if x.shape[-1] != 1 << self.n:
             raise ValueError("last dimension must hold 2^n elements")
         rows_total = x.numel() // x.shape[-1]
         b = rows_total.bit_length() - 1
         if rows_total != 1 << b:
             raise ValueError("leading dimensions must hold a power-of-two count of rows")
-        stages, final = self._plans_for(elem_bytes, b)
         if stream is None:
             stream = torch.cuda.current_stream(x.device)
         src = x.contiguous()
+        if self.fused:
+            sp = self._sort_plan(key, b)
+            out = torch.empty_like(src)
+            ws = torch.empty(sp.ws_bytes, dtype=torch.uint8, device=x.device) \
+                if sp.ws_bytes else None
+            with torch.cuda.device(x.device):
+                B.bmmc_sort_execute(sp.h, src.data_ptr(), out.data_ptr(),
+                                    ws.data_ptr() if ws is not None else None,
+                                    stream.cuda_stream)
+            return out
+        stages, final = self._plans_for(elem_bytes, b)
         bufs = [torch.empty_like(src), torch.empty_like(src)]
         cur = src
         with torch.cuda.device(x.device):
