@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--bp", type=int, default=16)
     ap.add_argument("--tiled", type=int, default=16)
     ap.add_argument("--strategy", choices=["paper", "single"], default="paper")
+    ap.add_argument("--cta-tile", type=int, default=0,
+                    help="log2 bytes per thread block of the headline plans (0 = default)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -785,7 +787,8 @@ def main():
     # ---- plans and device buffers (outside the timed region) --------------
     import workloads as wl
     items = workload(n, elems, args.bp, args.tiled, args.dense, seed_base=1000 * rank)
-    plans = [bm.Plan(n, rows, c, e, flags=flags) for (_, e, rows, c) in items]
+    plans = [bm.Plan(n, rows, c, e, flags=flags, cta_tile_log2=args.cta_tile)
+             for (_, e, rows, c) in items]
     bufs = {}
     for e in elems:
         x = wl.payload_torch(n, e, seed=rank, device=dev)

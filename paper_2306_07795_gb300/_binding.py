@@ -39,6 +39,9 @@ EXPORTED = (
     "bmmc_sort_plan_create", "bmmc_sort_plan_destroy", "bmmc_sort_plan_num_passes",
     "bmmc_sort_workspace_bytes", "bmmc_sort_execute", "bmmc_sort_plan_emulate",
     "bmmc_sort_plan_describe",
+    # include/bmmc_shard.h
+    "bmmc_shard_plan_create", "bmmc_shard_plan_destroy", "bmmc_shard_plan_num_steps",
+    "bmmc_shard_plan_step", "bmmc_shard_plan_verify",
     # include/bmmc_batch.h
     "bmmc_batch_workspace_bytes", "bmmc_batch_table_bytes", "bmmc_batch_create",
     "bmmc_batch_execute",
@@ -140,6 +143,13 @@ def lib():
         "bmmc_sort_execute": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bmmc_sort_plan_emulate": (ctypes.c_int, [vp, vp, vp]),
         "bmmc_sort_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "bmmc_shard_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int,
+                                                  ctypes.c_int, u64p, ctypes.c_uint64]),
+        "bmmc_shard_plan_destroy": (None, [vp]),
+        "bmmc_shard_plan_num_steps": (ctypes.c_int, [vp]),
+        "bmmc_shard_plan_step": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_int), u64p, u64p]),
+        "bmmc_shard_plan_verify": (ctypes.c_int, [vp]),
         "bmmc_batch_workspace_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_table_bytes": (ctypes.c_size_t, [vpp, ctypes.c_int]),
         "bmmc_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), vpp, ctypes.c_int,
@@ -356,6 +366,45 @@ def bmmc_sort_plan_describe(h):
     buf = ctypes.create_string_buffer(need + 1)
     lib().bmmc_sort_plan_describe(h, buf, need + 1)
     return json.loads(buf.value.decode())
+
+
+# ---------------------------------------------------------------------------
+# include/bmmc_shard.h
+# ---------------------------------------------------------------------------
+
+BMMC_SHARD_LOCAL = 0
+BMMC_SHARD_EXCHANGE = 1
+
+
+def bmmc_shard_plan_create(n, g, rows, c):
+    h = ctypes.c_void_p()
+    _check(lib().bmmc_shard_plan_create(ctypes.byref(h), n, g, _rows(rows), c),
+           "bmmc_shard_plan_create")
+    return h
+
+
+def bmmc_shard_plan_destroy(h):
+    lib().bmmc_shard_plan_destroy(h)
+
+
+def bmmc_shard_plan_num_steps(h):
+    return lib().bmmc_shard_plan_num_steps(h)
+
+
+def bmmc_shard_plan_step(h, i, rank, nl):
+    """(kind, rows, c) of step i on rank `rank`; rows has nl = n - g masks."""
+    kind = ctypes.c_int()
+    rows = (ctypes.c_uint64 * max(1, nl))()
+    c = ctypes.c_uint64()
+    _check(lib().bmmc_shard_plan_step(h, i, rank, ctypes.byref(kind), rows, ctypes.byref(c)),
+           "bmmc_shard_plan_step")
+    if kind.value == BMMC_SHARD_EXCHANGE:
+        return kind.value, None, None
+    return kind.value, [int(r) for r in rows[:nl]], int(c.value)
+
+
+def bmmc_shard_plan_verify(h):
+    return lib().bmmc_shard_plan_verify(h)
 
 
 # ---------------------------------------------------------------------------

@@ -88,3 +88,75 @@ def test_reference_arm_reports_our_config(monkeypatch, capsys):
     assert line["cpu_baseline"]["value"] == line["value"] > 0
     assert "n = 12" in line["cpu_baseline"]["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _shard_main(rank, world, port, n, cases, q):
+    """One rank of a sharded BMMC over gloo: local steps through the oracle's
+    C loop (a CPU stand-in for the kernels), exchanges through gloo's
+    all_to_all_single; the result shards are gathered on rank 0."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2306_07795_gb300.shard import ShardedPlan
+        import workloads as wl
+        g = world.bit_length() - 1
+        nl = n - g
+        out = []
+        for rows, c, e in cases:
+            full = wl.payload(n, e, seed=7)
+            flat = np.ascontiguousarray(full).reshape(-1).view(np.int32)
+            per = flat.size >> g
+            mine = torch.from_numpy(flat[rank * per:(rank + 1) * per].copy())
+
+            def local(lrows, lc, x):
+                arr = np.ascontiguousarray(x.numpy()).reshape(-1)
+                y = oracle.apply(nl, lrows, lc, arr, elem_bytes=e)
+                return torch.from_numpy(y).view(x.shape)
+
+            res = ShardedPlan(n, g, rows, c, elem_bytes=e)(mine, rank, local=local)
+            parts = [torch.empty_like(res) for _ in range(world)]
+            dist.all_gather(parts, res)
+            if rank == 0:
+                got = torch.cat(parts).numpy()
+                want = oracle.apply(n, rows, c, full, elem_bytes=e)
+                want = np.ascontiguousarray(want).reshape(-1).view(np.int32)
+                out.append(bool(np.array_equal(got, want)))
+        q.put((rank, out))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_sharded_bmmc_gloo(world):
+    """A BMMC of one array spread over 2 and 4 gloo ranks equals the oracle
+    on the whole array, bit for bit (dense matrices with one and two
+    exchanges, bit-reversal, 4- and 16-byte elements)."""
+    from oracle import f2
+    import workloads as wl
+    n = 12
+    inv = lambda rows: f2.is_invertible(rows, n)  # noqa: E731
+    cases = [wl.dense_bmmc(n, 1, inv) + (4,), wl.dense_bmmc(n, 2, inv) + (16,),
+             (wl.bit_reverse(n), 0, 4)]
+    g = world.bit_length() - 1
+    low = (1 << (n - g)) - 1
+    # whole shards change rank: no low bit reaches the rank bits (two exchanges)
+    lr, lc = wl.dense_bmmc(n - g, 3, lambda r: f2.is_invertible(r, n - g))
+    top = [1 << (n - 1 - i) for i in range(g)]
+    cases.append((list(lr) + top, (lc & low) | (1 << (n - g)), 8))
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_main, args=(r, world, port, n, cases, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    results = dict(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert results[0] == [True] * len(cases)
