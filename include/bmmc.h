@@ -76,12 +76,21 @@ enum bmmc_plan_flags {
      * holds whole input segments and whole output segments whatever A is.
      * This goes beyond the paper, whose tiles are always spanned by unit
      * vectors; the result is the same permutation. */
-    BMMC_PLAN_SINGLE_PASS = 1
+    BMMC_PLAN_SINGLE_PASS = 1,
+    /* A flag added to either strategy: thread blocks load their input
+     * segments with tensor copies (TMA, cp.async.bulk.tensor, one per
+     * 128-byte-line run of a segment) into shared memory swizzled by the
+     * hardware's 128-byte pattern, instead of 16-byte cp.async copies per
+     * thread.  A pass takes it where the gathers stay free of bank conflicts
+     * under that fixed swizzle, and keeps the 16-byte copies otherwise
+     * (bmmc_plan_describe reports which).  Same permutation, bit for bit. */
+    BMMC_PLAN_TMA_LOAD = 2
 };
 
 /* Tuning knobs.  Zero in a field selects the library default. */
 typedef struct bmmc_plan_options {
-    uint32_t flags;      /* a bmmc_plan_flags value */
+    uint32_t flags;      /* a strategy of bmmc_plan_flags, optionally with
+                            BMMC_PLAN_TMA_LOAD */
     int seg_bits;        /* log2 of the elements in one contiguous segment
                             (the paper's n_tile); must satisfy
                             2^seg_bits * elem_bytes >= 128 */
@@ -307,6 +316,18 @@ int bmmc_plan_verify(bmmc_plan p, uint64_t max_ctas);
  * buf (NUL-terminated, truncated to len).  Returns the full length needed,
  * or a negative code. */
 int bmmc_plan_describe(bmmc_plan p, char *buf, size_t len);
+
+/*
+ * Bounded waits that gave up on the current device since the library was
+ * loaded.  A pass that loads its tiles by tensor copies (BMMC_PLAN_TMA_LOAD)
+ * waits for them on a shared-memory barrier for at most about a second; if
+ * the copies have not landed by then, the thread block counts it here and
+ * ends without writing its part of the output, instead of waiting forever.
+ * 0 means no execution hit that limit.  A host-side check for callers that
+ * want to detect such a failure; no counterpart in the paper.
+ * Errors: INVALID (NULL), CUDA.
+ */
+int bmmc_device_wait_timeouts(unsigned long long *count);
 
 /* A static, human-readable name for a status code. */
 const char *bmmc_strerror(int code);

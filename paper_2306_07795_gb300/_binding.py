@@ -25,6 +25,7 @@ BMMC_STATIC_SCRATCH_BYTES = 32 << 20
 
 BMMC_PLAN_PAPER = 0
 BMMC_PLAN_SINGLE_PASS = 1
+BMMC_PLAN_TMA_LOAD = 2
 
 # Every entry point declared in include/bmmc.h (checked by the tests).
 EXPORTED = (
@@ -34,7 +35,7 @@ EXPORTED = (
     "bmmc_plan_workspace_bytes", "bmmc_execute", "bmmc_execute_ws", "bmmc_execute_host",
     "bmmc_execute_static_ws", "bmmc_plan_verify", "bmmc_plan_describe",
     "bmmc_strerror", "bmmc_plan_compose", "bmmc_parm_matrix", "bmmc_execute_ce",
-    "bmmc_plan_lift", "bmmc_sort_schedule",
+    "bmmc_plan_lift", "bmmc_sort_schedule", "bmmc_device_wait_timeouts",
     # include/bmmc_sort.h
     "bmmc_sort_plan_create", "bmmc_sort_plan_destroy", "bmmc_sort_plan_num_passes",
     "bmmc_sort_workspace_bytes", "bmmc_sort_execute", "bmmc_sort_plan_emulate",
@@ -132,6 +133,7 @@ def lib():
         "bmmc_execute_ce": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, vp]),
         "bmmc_parm_matrix": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, u64p]),
         "bmmc_plan_lift": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp)]),
+        "bmmc_device_wait_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong)]),
         "bmmc_sort_schedule": (ctypes.c_int, [ctypes.c_int, u64p, ctypes.c_int, u64p,
                                               ctypes.POINTER(ctypes.c_int)]),
         "bmmc_sort_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int,
@@ -301,6 +303,12 @@ BMMC_KEY_I64, BMMC_KEY_U64, BMMC_KEY_F64 = 4, 5, 6
 def bmmc_execute_ce(h, in_ptr, out_ptr, ws_ptr, key_type, stream=0):
     _check(lib().bmmc_execute_ce(h, in_ptr, out_ptr, ws_ptr, key_type, stream),
            "bmmc_execute_ce")
+
+
+def bmmc_device_wait_timeouts():
+    n = ctypes.c_ulonglong()
+    _check(lib().bmmc_device_wait_timeouts(ctypes.byref(n)), "bmmc_device_wait_timeouts")
+    return int(n.value)
 
 
 def bmmc_plan_lift(h, b):

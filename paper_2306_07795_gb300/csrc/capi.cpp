@@ -17,6 +17,7 @@
 namespace bmmc {
 cudaError_t launch_pass(const PassDesc &d, const void *in, void *out, cudaStream_t s,
                         int key);
+cudaError_t device_wait_timeouts(unsigned long long *count);
 }
 
 using namespace bmmc;
@@ -61,8 +62,10 @@ int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
     if (opts) {
         for (int r : opts->reserved)
             if (r) return BMMC_ERR_UNSUPPORTED;
-        if (opts->flags > BMMC_PLAN_SINGLE_PASS) return BMMC_ERR_UNSUPPORTED;
+        if (opts->flags & ~(uint32_t)(BMMC_PLAN_SINGLE_PASS | BMMC_PLAN_TMA_LOAD))
+            return BMMC_ERR_UNSUPPORTED;
         opt.flags = opts->flags;
+        opt.swizzle128 = (opts->flags & BMMC_PLAN_TMA_LOAD) != 0;
         opt.seg_bits = opts->seg_bits;
         opt.cta_tile_log2 = opts->cta_tile_log2;
         opt.tile_order = opts->tile_order;
@@ -95,7 +98,7 @@ int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
     int k = opt.seg_bits ? opt.seg_bits : default_seg_bits(e_log);
     if (k > n) k = n;
     const bool small = ((1ull << (n + e_log)) <= kWholeArrayBytes);
-    if (small || opt.flags == BMMC_PLAN_SINGLE_PASS || f2::tiled_columns(a, k)) {
+    if (small || (opt.flags & BMMC_PLAN_SINGLE_PASS) || f2::tiled_columns(a, k)) {
         p->npass = 1;
         p->t[0] = a;
         p->tc[0] = c;
@@ -113,6 +116,13 @@ int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
     }
     for (int i = 0; i < p->npass; ++i) {
         int rc = derive_pass(p->t[i], p->tc[i], n, e_log, opt, &p->desc[i], &p->info[i]);
+        if (rc == 0 && opt.swizzle128 && !p->desc[i].tma) {
+            // the fixed swizzle did not give conflict-free gathers: this pass
+            // keeps the searched swizzle and 16-byte copies
+            PlanOptions o2 = opt;
+            o2.swizzle128 = false;
+            rc = derive_pass(p->t[i], p->tc[i], n, e_log, o2, &p->desc[i], &p->info[i]);
+        }
         if (rc) {
             delete p;
             return rc;
@@ -333,6 +343,16 @@ int bmmc_execute_ce(bmmc_plan p, const void *in, void *out, void *ws, int key_ty
     return execute_impl(p, in, out, ws, (cudaStream_t)stream, key_type);
 }
 
+int bmmc_device_wait_timeouts(unsigned long long *count)
+{
+    if (!count) return BMMC_ERR_INVALID;
+    if (device_wait_timeouts(count) != cudaSuccess) {
+        cudaGetLastError();
+        return BMMC_ERR_CUDA;
+    }
+    return BMMC_OK;
+}
+
 int bmmc_plan_verify(bmmc_plan p, uint64_t max_ctas)
 {
     return guarded([&] { return verify_impl(p, max_ctas); });
@@ -378,7 +398,7 @@ int describe_impl(bmmc_plan p, char *buf, size_t len)
     std::string s = "{\"n\": " + std::to_string(p->n) +
                     ", \"elem_bytes\": " + std::to_string(1 << p->e_log) +
                     ", \"strategy\": \"" +
-                    (p->opt.flags == BMMC_PLAN_SINGLE_PASS ? "single_pass" : "paper") +
+                    ((p->opt.flags & BMMC_PLAN_SINGLE_PASS) ? "single_pass" : "paper") +
                     "\", \"passes\": [";
     for (int i = 0; i < p->npass; ++i) {
         const PassDesc &d = p->desc[i];
@@ -390,12 +410,12 @@ int describe_impl(bmmc_plan p, char *buf, size_t len)
                  "\"threads\": %u, \"loop\": %u, \"smem_bytes\": %u, "
                  "\"wavefronts_load\": %d, \"ideal_load\": %d, \"wavefronts_store\": %d, "
                  "\"ideal_store\": %d, \"lanes34\": [%d, %d], \"rot\": %d, "
-                 "\"sigma\": [%u, %u, %u]}",
+                 "\"sigma\": [%u, %u, %u], \"tma\": %u}",
                  i ? ", " : "", d.naive, f.tiled, d.k, d.m, f.n_over, d.it,
                  (unsigned long long)(1ull << d.n_cta), 1u << d.thread_bits, d.loop,
                  d.smem_bytes, f.wavefronts_load, f.ideal_load, f.wavefronts_store,
                  f.ideal_store, f.lane3, f.lane4, f.rot, f.sigma[0], f.sigma[1],
-                 f.sigma[2]);
+                 f.sigma[2], d.tma);
         s += tmp;
     }
     s += "]}";

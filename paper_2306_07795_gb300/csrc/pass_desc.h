@@ -28,6 +28,7 @@ namespace bmmc {
 constexpr int kMaxN = 32;        // index bits
 constexpr int kMaxThreadBits = 8;  // 256 threads per block
 constexpr int kMaxLoop = 64;     // chunks per thread per phase
+constexpr int kMaxSegBits = 12;  // input segments per block = 2^(m + it)
 
 struct PassDesc {
     // ---- shape -------------------------------------------------------------
@@ -41,6 +42,9 @@ struct PassDesc {
     uint32_t loop;         // chunks per thread in each phase
     uint32_t smem_bytes;   // shared memory per block
     uint32_t naive;        // 1: tiny array, one block, direct index map
+    uint32_t tma;          // 1: phase 1 by tensor copies, one per input
+                           //    segment, into shared memory swizzled by the
+                           //    hardware 128-byte pattern (the tables' swizzle)
     // ---- per thread-block bit b (b < n_cta) -------------------------------
     uint32_t cta_in[kMaxN];   // input element offset
     uint32_t cta_out[kMaxN];  // output element offset
@@ -58,6 +62,8 @@ struct PassDesc {
     uint32_t loop_dst[kMaxLoop];
     uint32_t loop_src[kMaxLoop];
     uint32_t loop_out[kMaxLoop];
+    // ---- per segment bit b (b < m + it): input offset of segment 2^b ----
+    uint32_t seg_in[kMaxSegBits];
     // ---- per element j of an output chunk (j < 16 / elem bytes) ----------
     uint32_t elem_src[4];     // shared-memory slot offset of element j
     // ---- naive path (naive == 1): the matrix itself ------------------------

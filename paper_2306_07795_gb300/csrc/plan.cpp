@@ -105,12 +105,38 @@ int wavefronts(const uint32_t *delta_words, int group_bits)
 int derive_pass(const f2::Mat &t, uint64_t c, int n, int e_log,
                 const PlanOptions &opt, PassDesc *desc, PassInfo *info)
 {
-    return derive_pass_span(t, c, n, e_log, opt, nullptr, 0, desc, info, nullptr);
+    int rc = derive_pass_span(t, c, n, e_log, opt, nullptr, 0, desc, info, nullptr);
+    if (rc || !opt.swizzle128 || desc->naive || desc->m < 2 ||
+        info->wavefronts_store <= info->ideal_store)
+        return rc;
+    // The hardware swizzle spreads the tile's row bits 0 and 1 over the
+    // banks: try every ordered pair of tile rows in those places and keep
+    // the ordering with the fewest wavefronts.
+    const int m = (int)desc->m;
+    PassDesc d2;
+    PassInfo i2;
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            if (a == b || (a == 0 && b == 1)) continue;
+            uint8_t order[64];
+            int o = 0;
+            order[o++] = (uint8_t)a;
+            order[o++] = (uint8_t)b;
+            for (int j = 0; j < m; ++j)
+                if (j != a && j != b) order[o++] = (uint8_t)j;
+            if (derive_pass_span(t, c, n, e_log, opt, nullptr, 0, &d2, &i2, nullptr, order) == 0 &&
+                d2.tma && (!desc->tma || i2.wavefronts_store < info->wavefronts_store)) {
+                *desc = d2;
+                *info = i2;
+                if (info->wavefronts_store <= info->ideal_store) return 0;
+            }
+        }
+    return rc;
 }
 
 int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
                      const PlanOptions &opt, const uint64_t *span, int span_count,
-                     PassDesc *desc, PassInfo *info, SlotMap *map)
+                     PassDesc *desc, PassInfo *info, SlotMap *map, const uint8_t *row_order)
 {
     PassDesc &d = *desc;
     memset(&d, 0, sizeof(d));
@@ -174,6 +200,19 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
                 int tp = piv[a]; piv[a] = piv[b]; piv[b] = tp;
                 uint64_t tv = rowv[a]; rowv[a] = rowv[b]; rowv[b] = tv;
             }
+    // or in the order asked for (row bit j = sorted row row_order[j])
+    if (row_order) {
+        int pv[64];
+        uint64_t rv[64];
+        for (int j = 0; j < m; ++j) {
+            pv[j] = piv[row_order[j]];
+            rv[j] = rowv[row_order[j]];
+        }
+        for (int j = 0; j < m; ++j) {
+            piv[j] = pv[j];
+            rowv[j] = rv[j];
+        }
+    }
     // Tile position of v in V: row r from the pivot bits of hi(v), column
     // l = lo(v).  Valid for v in V only.
     bool phi_ok = true;
@@ -432,7 +471,11 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
         sw.w_log = w_log;
         int tries = 0;
         const bool can_reach = within_chunk_rank(cd) == w_log;
-        const int max_tries = can_reach ? 2 + (line_mask ? 48 : 0) : 1;
+        int max_tries = can_reach ? 2 + (line_mask ? 48 : 0) : 1;
+        if (opt.swizzle128) {  // only the hardware pattern
+            tries = 1;
+            max_tries = 2;
+        }
         for (; tries < max_tries; ++tries) {
             if (tries == 0) {
                 sw.sigma[0] = sw.sigma[1] = sw.sigma[2] = 0;
@@ -503,6 +546,21 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
         d.loop_out[i] = xor_of(l_out.data(), i);
     }
     for (uint32_t j = 0; j < (1u << w_log); ++j) d.elem_src[j] = sw(xor_of(lo_p, j));
+    // Segment s of the block (bits: tile rows, then tiles) starts at slot
+    // s << k and at input offset block base + xor of seg_in over the bits of
+    // s: the chunk-index bits above the k - w_log column-chunk bits.
+    if (m + it <= kMaxSegBits)
+        for (int b = 0; b < m + it; ++b) d.seg_in[b] = ic_in[k - w_log + b];
+    // Tensor copies: the swizzle is the 128-byte hardware pattern, the gathers
+    // under it take at most twice the ideal wavefronts (the pass is bound by
+    // DRAM, and a 2-way conflict in the gathers costs far less than the
+    // tile's DRAM time), every segment is whole 128-byte lines (at most 256
+    // of them, one copy's box), and the segment count fits the table.
+    const bool hw_pattern = sw.sigma[0] == ((P > w_log + 3) ? (1u << (w_log + 3)) : 0u) &&
+                            sw.sigma[1] == ((P > w_log + 4) ? (1u << (w_log + 4)) : 0u) &&
+                            sw.sigma[2] == ((P > w_log + 5) ? (1u << (w_log + 5)) : 0u);
+    d.tma = (opt.swizzle128 && hw_pattern && best_wf <= 2 * ideal_store && k + e_log >= 7 &&
+             k + e_log - 7 <= 8 && P >= w_log + 6 && m + it <= kMaxSegBits) ? 1u : 0u;
 
     // diagnostics
     {
@@ -525,6 +583,7 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
     info->lane4 = best.l4;
     info->rot = (best.rot_lane[0] >= 0 ? 1 : 0) + (best.rot_lane[1] >= 0 ? 2 : 0);
     for (int q = 0; q < 3; ++q) info->sigma[q] = sw.sigma[q];
+    info->swizzle128 = opt.swizzle128 ? 1 : 0;
     return 0;
 }
 
@@ -587,6 +646,25 @@ int verify_pass(const PassDesc &d, const f2::Mat &t, uint64_t c,
         }
         for (uint32_t s = 0; s < slots; ++s)
             if (slot_src[s] == -1) return fail("slot never written");
+        if (d.tma) {
+            // the tensor copies put input base + seg(s) + col at the 128-byte
+            // swizzle of slot (s << k) + col
+            const uint32_t wl = 4 - d.e_log;
+            uint32_t base = 0;
+            for (uint32_t b = 0; b < d.n_cta; ++b)
+                if ((g >> b) & 1ull) base ^= d.cta_in[b];
+            for (uint32_t sg = 0; sg < (1u << (d.m + d.it)); ++sg) {
+                uint32_t off = base;
+                for (uint32_t b = 0; b < d.m + d.it; ++b)
+                    if ((sg >> b) & 1u) off ^= d.seg_in[b];
+                for (uint32_t col = 0; col < (1u << d.k); ++col) {
+                    const uint32_t p = (sg << d.k) | col;
+                    const uint32_t phys = p ^ (((p >> (wl + 3)) & 7u) << wl);
+                    if (phys >= slots || slot_src[phys] != (int64_t)(off ^ col))
+                        return fail("tensor copy placement");
+                }
+            }
+        }
         for (uint32_t tid = 0; tid < threads; ++tid) {
             ThreadBase tb = thread_base(d, (uint32_t)g, tid);
             for (uint32_t i = 0; i < d.loop; ++i) {

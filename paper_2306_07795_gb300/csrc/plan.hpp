@@ -12,10 +12,14 @@
 namespace bmmc {
 
 struct PlanOptions {
-    uint32_t flags = 0;     // 0 = paper (1 or 2 tiled passes), 1 = single pass
+    uint32_t flags = 0;     // strategy (0 = paper, 1 = single pass) | load flag
     int seg_bits = 0;       // 0 = default for the element size
     int cta_tile_log2 = 0;  // 0 = default (16 KiB per thread block)
     int tile_order = 0;     // 0 = default, 1 = natural, 2 = interleaved
+    // The shared-memory swizzle fixed to the hardware 128-byte pattern (chunk
+    // bit q of a 128-byte line flipped by line bit q), the layout a tensor
+    // copy with 128-byte swizzling writes.
+    bool swizzle128 = false;
 };
 
 // Diagnostics of one pass, reported by bmmc_plan_describe.
@@ -27,6 +31,7 @@ struct PassInfo {
     int ideal_load = 0, ideal_store = 0;
     int lane3 = -1, lane4 = -1, rot = 0;
     uint32_t sigma[3] = {0, 0, 0};
+    int swizzle128 = 0;        // the swizzle is the 128-byte hardware pattern
 };
 
 // Derive the launch tables of one pass out[T x + c] = in[x].
@@ -58,9 +63,12 @@ struct SlotMap {
 // contain span[0..span_count) (plus the tile subspace V); the block then holds
 // 2^(k + m + it) elements with `it` set by the span, and the other index bits
 // become thread-block bits.  map (may be NULL) receives the slot map.
+// row_order (may be NULL): tile row bit j holds the j-th row of the
+// pivot-sorted basis given; used to fit the hardware swizzle.
 int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
                      const PlanOptions &opt, const uint64_t *span, int span_count,
-                     PassDesc *desc, PassInfo *info, SlotMap *map);
+                     PassDesc *desc, PassInfo *info, SlotMap *map,
+                     const uint8_t *row_order = nullptr);
 
 // Walk the tables of a pass on the host (see bmmc_plan_verify).  Returns 0 if
 // every check passes.

@@ -444,16 +444,22 @@ void worker_main(bmmc_server_s *s)
     // across turns so that a failed host allocation loses none of them.
     std::deque<Req *> fresh;
     for (;;) {
-        bool busy;
+        // blocked: requests wait for admission (poll completions at once);
+        // busy: launches in flight (retire them, but no hurry: latency comes
+        // from CUDA events, and polling beside the submitting thread slows its
+        // launches)
+        bool busy, blocked;
         {
             std::lock_guard<std::mutex> lk2(s->sched_mu);
-            busy = !s->waiting.empty() || s->n_inflight != 0 || !fresh.empty();
+            blocked = !s->waiting.empty() || !fresh.empty();
+            busy = blocked || s->n_inflight != 0;
         }
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            if ((!busy && s->submitted.empty()) || (s->hold && !s->stop)) {
+            if ((!blocked && s->submitted.empty()) || (s->hold && !s->stop)) {
                 if (s->stop && s->submitted.empty() && !busy) return;
-                s->cv.wait_for(lk, std::chrono::milliseconds(1));
+                if (busy) s->cv.wait_for(lk, std::chrono::microseconds(100));
+                else s->cv.wait_for(lk, std::chrono::milliseconds(1));
                 if (s->hold && !s->stop) {
                     lk.unlock();
                     std::lock_guard<std::mutex> lk2(s->sched_mu);
@@ -664,15 +670,23 @@ int bmmc_server_submit(bmmc_server s, uint64_t id, int n, const uint64_t *A_rows
             bool launched = false;
             if (s->waiting.empty()) {
                 const int prev = enter_device(s);
-                retire(s);
+                // launch first; retire finished launches after it (or before
+                // a second try when the budget or the arena was full), so that
+                // their bookkeeping does not delay this request
                 launched = admit_one(s, r);
+                retire(s);
+                if (!launched) launched = admit_one(s, r);
                 if (prev >= 0) cudaSetDevice(prev);
             }
             if (!launched) s->waiting.push_back(r);
             if (launched) s->n_inline += 1;
             lk2.unlock();
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->cv.notify_one();  // the scheduler retires the launch, or admits r
+            if (!launched) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->cv.notify_one();  // the scheduler admits r when room frees
+            }
+            // a launched request is retired by the scheduler's next turn (at
+            // most 100 us away) or by the next submission
             return BMMC_OK;
         }
         // PLAIN: allocate (waiting for completions if the arena is full), launch.

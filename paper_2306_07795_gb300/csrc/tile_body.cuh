@@ -53,6 +53,65 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// ---- tensor copies (TMA) completing on a shared-memory mbarrier ----------
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// One arrival that also expects `bytes` more bytes of asynchronous copies.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait for the barrier phase of parity `parity` for at most about a second;
+// false if it has not completed by then.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+// A 2-D tensor copy global -> shared of one box at coordinates (c0, c1),
+// completing on `bar` (the tensor map describes the box and the swizzle).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int32_t c0,
+                                            int32_t c1, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ uint32_t lds32(uint32_t addr)
 {
     uint32_t v;
@@ -192,6 +251,34 @@ __device__ __forceinline__ void tile_load(const PassDesc &d, const TileAddr &a,
         const uint32_t s = a.dst ^ d.loop_dst[i];
         cp_async_16(sbase + (s << E_LOG), in + ((uint64_t)g << E_LOG));
     }
+}
+
+// Phase 1 by tensor copies: each input segment of the block (whole 128-byte
+// lines, the box of the 2-D tensor map over the array as lines of 32 words)
+// is one copy into its place in the tile, swizzled by the hardware 128-byte
+// pattern the tables were derived for.  Thread 0 arrives on `bar` expecting
+// all the bytes; every thread then waits for the barrier (at most about a
+// second: false if the copies did not all land by then).
+template <int E_LOG>
+__device__ __forceinline__ bool tile_load_tma(const PassDesc &d, const void *tmap,
+                                              uint32_t cta, uint32_t sbase, uint32_t bar)
+{
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31u;
+    const bool bit = (lane < d.n_cta) && ((cta >> lane) & 1u);
+    const uint32_t base = __reduce_xor_sync(0xffffffffu, bit ? d.cta_in[lane] : 0u);
+    const uint32_t seg_bits = d.m + d.it;
+    const uint32_t seg_log = d.k + E_LOG;  // log2 bytes of a segment
+    if (tid == 0) mbar_arrive_expect_tx(bar, 1u << (seg_bits + seg_log));
+    for (uint32_t s = tid; s < (1u << seg_bits); s += blockDim.x) {
+        uint32_t off = base;
+#pragma unroll
+        for (int b = 0; b < kMaxSegBits; ++b)
+            if (b < (int)seg_bits && ((s >> b) & 1u)) off ^= d.seg_in[b];
+        const int32_t line = (int32_t)(((uint64_t)off << E_LOG) >> 7);
+        tma_load_2d(sbase + (s << seg_log), tmap, 0, line, bar);
+    }
+    return mbar_wait_bounded(bar, 0);
 }
 
 // Phase 2: shared memory -> this thread's output chunks.

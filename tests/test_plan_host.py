@@ -241,3 +241,39 @@ def test_random_dense_factors_have_no_overlap():
         overlaps += sum(ps["n_over"] != 0 for ps in p.describe()["passes"])
     assert tiled == 0
     assert overlaps <= 3, overlaps  # at most 3 of 120 factor passes
+
+
+@pytest.mark.parametrize("e", [4, 8, 16])
+def test_tma_load_plans_verify(e):
+    """Plans with tensor-copy tile loads: the host walk of every index checks
+    that the copies (one per input segment, hardware 128-byte swizzle) put
+    every input element where the gathers read it."""
+    from tests_common_classes import classes_for
+    used = 0
+    for n in (7, 10, 13, 16, 19):
+        for name, rows, c in classes_for(n, e, 7 * n):
+            for strat in (bm.BMMC_PLAN_PAPER, bm.BMMC_PLAN_SINGLE_PASS):
+                p = bm.Plan(n, rows, c, e, flags=strat | bm.BMMC_PLAN_TMA_LOAD)
+                assert p.verify() == 0, (n, e, name)
+                d = p.describe()
+                used += sum(ps["tma"] for ps in d["passes"])
+                for ps in d["passes"]:
+                    if ps["tma"]:
+                        assert ps["wavefronts_store"] <= 2 * ps["ideal_store"]
+    assert used > 0
+
+
+def test_tma_flag_keeps_the_permutation():
+    """The flag changes only how a tile is loaded: passes, matrices and the
+    verified tables of each pass still compose to A."""
+    n, e = 18, 4
+    rows, c = wl.dense_bmmc(n, 3, oracle_invertible)
+    a = bm.Plan(n, rows, c, e)
+    b = bm.Plan(n, rows, c, e, flags=bm.BMMC_PLAN_TMA_LOAD)
+    assert a.num_passes == b.num_passes == 2
+    assert a.pass_matrices() == b.pass_matrices()
+    assert b.verify() == 0
+    assert all(ps["tma"] == 1 for ps in b.describe()["passes"])
+    with pytest.raises(bm.BmmcError) as ei:
+        bm.Plan(n, rows, c, e, flags=4)
+    assert ei.value.code == bm.BMMC_ERR_UNSUPPORTED
