@@ -728,11 +728,11 @@ def bench_serving(dev, seconds=10.0, rate=2000.0, seed=11, budget=40 * 10**9, st
             d[f] = round(d[f], 4)
         return d
 
-    def compare(flags, speedup=1.0, limit_s=None, repeated=False):
+    def compare(flags, speedup=1.0, limit_s=None, repeated=False, large_log2=0):
         out = {}
         for mode, key in (("continuous", "server"), ("plain", "plain")):
             srv = serving.Server(dev, mode=mode, streams=streams, budget_bytes=budget,
-                                 flags=flags)
+                                 flags=flags, large_log2=large_log2 if mode != "plain" else 0)
             reqs = serving.drive(srv, requests(speedup, limit_s, repeated))
             out[key] = rounded(serving.summarize(reqs))
             out[key]["stats"] = srv.stats()
@@ -762,6 +762,9 @@ def bench_serving(dev, seconds=10.0, rate=2000.0, seed=11, budget=40 * 10**9, st
                                "peak_gbs": peak}
     res.update(compare(bm.BMMC_PLAN_PAPER))
     res["single_pass_plans"] = compare(bm.BMMC_PLAN_SINGLE_PASS)
+    # Extra: requests of 256 MiB and more on a high-priority stream
+    res["extra_priority_large"] = {"large_log2": 28}
+    res["extra_priority_large"].update(compare(bm.BMMC_PLAN_PAPER, large_log2=28))
     # Extra, beyond the configured 2000 requests/s: the same request mix with
     # arrival times compressed, 2 s per rate.
     res["extra_rate_sweep"] = []

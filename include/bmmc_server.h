@@ -53,7 +53,14 @@ typedef struct bmmc_server_config {
                                  same (n, A, c, elem_bytes); 0 = plan every
                                  request anew.  Entries in use are pinned; the
                                  least recently used free one is evicted */
-    int reserved[5];          /* must be zero */
+    int large_log2;           /* CONTINUOUS with S >= 2: requests whose array
+                                 holds at least 2^large_log2 bytes run on
+                                 stream 0, created with the highest priority;
+                                 the others spread over streams 1..S-1.  Small
+                                 requests that arrive while a large one runs
+                                 then fill only the SMs it leaves idle instead
+                                 of slowing it.  0 = every stream alike */
+    int reserved[4];          /* must be zero */
 } bmmc_server_config;
 
 /* One finished request. */

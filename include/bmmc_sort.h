@@ -33,8 +33,10 @@ extern "C" {
 typedef struct bmmc_sort_plan_s *bmmc_sort_plan;
 
 typedef struct bmmc_sort_options {
-    int block_log2;   /* log2 of the bytes one thread block holds; 0 = 64 KiB.
-                         Must leave room for 2^12 keys and be at most 64 KiB. */
+    int block_log2;   /* log2 of the bytes one thread block holds; 0 = up to
+                         64 KiB, smaller for arrays that would give a pass
+                         fewer than 512 thread blocks.  Must leave room for
+                         2^12 keys and be at most 64 KiB. */
     int reserved[7];  /* must be zero */
 } bmmc_sort_options;
 

@@ -65,7 +65,8 @@ class bmmc_server_config(ctypes.Structure):
                 ("budget_bytes", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
                 ("plan_flags", ctypes.c_uint32), ("group_max_bytes", ctypes.c_uint64),
                 ("group_min", ctypes.c_int), ("keep_outputs", ctypes.c_int),
-                ("plan_cache", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("plan_cache", ctypes.c_int), ("large_log2", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class bmmc_server_result(ctypes.Structure):

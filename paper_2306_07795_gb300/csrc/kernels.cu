@@ -150,14 +150,21 @@ cudaError_t launch_typed(const PassDesc &d, const void *in, void *out, cudaStrea
     if (d.naive)
         return launch_pdl(bmmc_naive_pass<E_LOG, KEY>, dim3(1), dim3(1u << d.n), 0, s, d, src,
                           dst);
+    // Tiles within the default 48 KiB of dynamic shared memory (the default
+    // 16 KiB ones) need no attribute, and so no device lookup per launch.
+    constexpr uint32_t kDefaultSmem = 48 * 1024;
     int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return err;
+    cudaError_t err = cudaSuccess;
+    const bool needs_attr = d.smem_bytes + (d.tma ? 1024u + 16u : 0u) > kDefaultSmem;
+    if (needs_attr) {
+        err = cudaGetDevice(&dev);
+        if (err != cudaSuccess) return err;
+    }
     if (d.tma) {
         CUtensorMap tmap;
         const uint64_t bytes = ((uint64_t)1 << d.n) << E_LOG;
         if (encode_lines_map(&tmap, in, bytes, 1u << (d.k + E_LOG - 7))) {
-            if (dev >= 0 && dev < kMaxDevices &&
+            if (needs_attr && dev >= 0 && dev < kMaxDevices &&
                 !g_attr_set_tma[dev][E_LOG - 2][KEY].load(std::memory_order_acquire)) {
                 err = cudaFuncSetAttribute(bmmc_tiled_pass_tma<E_LOG, KEY>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -171,7 +178,7 @@ cudaError_t launch_typed(const PassDesc &d, const void *in, void *out, cudaStrea
         }
         // no tensor-map encoder: the same tables through 16-byte copies
     }
-    if (dev >= 0 && dev < kMaxDevices &&
+    if (needs_attr && dev >= 0 && dev < kMaxDevices &&
         !g_attr_set[dev][E_LOG - 2][KEY].load(std::memory_order_acquire)) {
         err = cudaFuncSetAttribute(bmmc_tiled_pass<E_LOG, KEY>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);

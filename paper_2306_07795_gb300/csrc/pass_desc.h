@@ -27,7 +27,8 @@ namespace bmmc {
 
 constexpr int kMaxN = 32;        // index bits
 constexpr int kMaxThreadBits = 8;  // 256 threads per block
-constexpr int kMaxLoop = 64;     // chunks per thread per phase
+constexpr int kMaxLoop = 32;     // chunks per thread per phase (128 KiB tiles:
+                                 // 2^13 chunks over 256 threads)
 constexpr int kMaxSegBits = 12;  // input segments per block = 2^(m + it)
 
 struct PassDesc {

@@ -281,6 +281,18 @@ int least_loaded(bmmc_server_s *s)
     return best;
 }
 
+// The stream a request runs on: with large_log2 set, large requests on the
+// high-priority stream 0 and the others on the least loaded of the rest.
+int stream_for(bmmc_server_s *s, const Req *r)
+{
+    if (s->cfg.large_log2 <= 0 || s->nstreams < 2) return least_loaded(s);
+    if (r->array_bytes >= ((size_t)1 << s->cfg.large_log2)) return 0;
+    int best = 1;
+    for (int i = 2; i < s->nstreams; ++i)
+        if (s->inflight[i].size() < s->inflight[best].size()) best = i;
+    return best;
+}
+
 void note_peaks(bmmc_server_s *s)
 {
     s->peak_bytes = std::max<uint64_t>(s->peak_bytes, s->used);
@@ -405,9 +417,9 @@ bool admit(bmmc_server_s *s)
     if (group && launch_group(s, small, least_loaded(s))) {
         for (Req *r : admitted)
             if (r->array_bytes > s->cfg.group_max_bytes)
-                launch_single(s, r, least_loaded(s));
+                launch_single(s, r, stream_for(s, r));
     } else {
-        for (Req *r : admitted) launch_single(s, r, least_loaded(s));
+        for (Req *r : admitted) launch_single(s, r, stream_for(s, r));
     }
     note_peaks(s);
     return true;
@@ -421,7 +433,7 @@ bool admit_one(bmmc_server_s *s, Req *r)
     if (!idle && s->used + r->bytes > s->cfg.budget_bytes) return false;
     if (!allocate(s, r)) return false;
     s->used += r->bytes;
-    launch_single(s, r, least_loaded(s));
+    launch_single(s, r, stream_for(s, r));
     note_peaks(s);
     return true;
 }
@@ -598,8 +610,14 @@ int bmmc_server_create(bmmc_server *out, const bmmc_server_config *cfg)
             return BMMC_ERR_OOM;
         }
         s->arena.init(s->arena_mem, cfg->arena_bytes);
-        for (int i = 0; i < s->nstreams; ++i)
-            cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+        int prio_low = 0, prio_high = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+        for (int i = 0; i < s->nstreams; ++i) {
+            const bool high = i == 0 && s->cfg.large_log2 > 0 && s->nstreams >= 2 &&
+                              s->cfg.mode == BMMC_SERVER_CONTINUOUS;
+            cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking,
+                                         high ? prio_high : prio_low);
+        }
         for (int i = 0; i < 64; ++i) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) == cudaSuccess) s->events.push_back(e);

@@ -452,7 +452,14 @@ int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2)
     }
 
     const int k = default_seg_bits(e_log);
-    int D = (block_log2 ? block_log2 : 16) - e_log;
+    // Default block: 64 KiB (more stages per pass), but small enough that a
+    // pass has at least 512 thread blocks to spread over the SMs, and at
+    // least 2^12 keys.
+    int D = block_log2 ? block_log2 - e_log : 16 - e_log;
+    if (!block_log2) {
+        if (D > N - 9) D = N - 9;
+        if (D < kSortRegBits + 8) D = kSortRegBits + 8;
+    }
     if (D > N) D = N;
     if (D < kSortRegBits + 8 || D + e_log > 16 || D < 2 * k) return BMMC_ERR_UNSUPPORTED;
     p->block_bits = D;

@@ -52,7 +52,7 @@ class Request:
 class Server:
     def __init__(self, device, mode="continuous", streams=4, budget_bytes=40 * 10**9,
                  arena_bytes=None, flags=B.BMMC_PLAN_PAPER, group_max_bytes=1 << 22,
-                 group_min=4, keep_outputs=False, plan_cache=None):
+                 group_min=4, keep_outputs=False, plan_cache=None, large_log2=0):
         import torch
         self.device = torch.device(device)
         cfg = B.bmmc_server_config()
@@ -68,6 +68,8 @@ class Server:
         if plan_cache is None:
             plan_cache = 0 if mode == "plain" else 1024
         cfg.plan_cache = int(plan_cache)
+        # requests of at least 2^large_log2 bytes on a high-priority stream
+        cfg.large_log2 = int(large_log2)
         self.mode = mode
         with torch.cuda.device(self.device):
             self._h = B.bmmc_server_create(cfg)

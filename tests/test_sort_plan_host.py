@@ -115,9 +115,10 @@ def test_sorted_and_permutation_of_input():
 
 
 def test_pass_counts():
-    """Far fewer passes than the n (n + 1) / 2 of one pass per stage."""
+    """Far fewer passes than the n (n + 1) / 2 of one pass per stage, with
+    64 KiB blocks."""
     for n, most in ((16, 8), (20, 20), (24, 32)):
-        h = B.bmmc_sort_plan_create(n, 0, B.BMMC_KEY_F32)
+        h = B.bmmc_sort_plan_create(n, 0, B.BMMC_KEY_F32, 16)
         d = B.bmmc_sort_plan_describe(h)
         assert d["stages"] == n * (n + 1) // 2
         assert sum(p["stages"] for p in d["passes"]) == d["stages"]
