@@ -37,7 +37,12 @@ typedef struct bmmc_sort_options {
                          64 KiB, smaller for arrays that would give a pass
                          fewer than 512 thread blocks.  Must leave room for
                          2^12 keys and be at most 64 KiB. */
-    int reserved[7];  /* must be zero */
+    int compare_code; /* how a thread block runs its comparators: 0 = by
+                         block size, 1 = one compact loop (less code: faster
+                         for small, latency-bound sorts), 2 = a variant per
+                         comparator orientation (fewer instructions: faster
+                         for large sorts).  Same results either way. */
+    int reserved[6];  /* must be zero */
 } bmmc_sort_options;
 
 /*

@@ -83,7 +83,8 @@ class BmmcError(RuntimeError):
 
 
 class bmmc_sort_options(ctypes.Structure):
-    _fields_ = [("block_log2", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+    _fields_ = [("block_log2", ctypes.c_int), ("compare_code", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class bmmc_plan_options(ctypes.Structure):
@@ -342,9 +343,9 @@ def bmmc_parm_matrix(n, mask):
 # include/bmmc_sort.h
 # ---------------------------------------------------------------------------
 
-def bmmc_sort_plan_create(n, b, key_type, block_log2=0):
+def bmmc_sort_plan_create(n, b, key_type, block_log2=0, compare_code=0):
     h = ctypes.c_void_p()
-    o = bmmc_sort_options(block_log2)
+    o = bmmc_sort_options(block_log2, compare_code)
     _check(lib().bmmc_sort_plan_create(ctypes.byref(h), n, b, key_type, ctypes.byref(o)),
            "bmmc_sort_plan_create")
     return h

@@ -31,11 +31,23 @@ constexpr int kSortMaxGroups = 40;       // register groups in one pass
 constexpr int kSortMaxRoundBits = 6;     // rounds per group = 2^round_bits
 constexpr int kSortSmallMaxBits = 12;    // one-block sort: at most 2^12 keys
 constexpr int kSortSmallMaxStages = 78;  // 12 * 13 / 2
+constexpr int kSortUnrolledMinBits = 20; // unrolled compares from 2^20 4-byte keys
 
+// The low test of a stage: the element at physical slot q of the block
+// whose input base is x_b takes the smaller key of its pair iff
+// parity(hin & x_b) + parity(hslot & q) = 0.  The planner puts every lane,
+// warp and round vector of the stage's group in the kernel of hslot, so the
+// slot part depends only on the register index j: parity(hslot & reg_off(j))
+// = parity(j & hmask) for the j whose stage bit is 0.  Register j of every
+// thread of the block is thus the low one iff parity(j & hmask) equals the
+// block's bit parity(hin & x_b): one orientation pattern per block and
+// stage, known without any per-thread test.
 struct SortStage {
-    uint32_t hin;    // low test, input part: parity(hin & block input base)
-    uint16_t hslot;  // low test, slot part: parity(hslot & physical slot)
-    uint16_t jmask;  // parity(hslot & reg_off(j)) for j < 2^R, one bit per j
+    uint32_t hin;    // input part of the low test
+    uint16_t low0;   // bit j: register j is the low position when the block's
+                     // bit is 0 (parity(j & hmask) = 0); the complement when 1
+    uint8_t hmask;   // register bits t != k with parity(hslot & reg[t]) = 1
+    uint8_t pad;
 };
 
 struct SortGroup {
@@ -48,6 +60,9 @@ struct SortGroup {
 
 struct SortDesc {
     uint32_t key;          // bmmc_key_type of the keys
+    uint32_t unrolled;     // 1: each stage runs a variant with its orientation
+                           //    fixed at compile time (3 instructions per pair,
+                           //    more code); 0: one loop reading low0 (6 per pair)
     uint32_t n_stage;
     uint32_t n_group;
     uint32_t round_bits;   // rounds per group = 2^round_bits

@@ -62,8 +62,9 @@ __device__ __forceinline__ bool keep(V a, V b)
     else return dev::keep_pair64<KEY>((uint64_t)a, (uint64_t)b);
 }
 
-// One stage on the registers: pairs (j, j + 2^I); bit j of `low` tells
-// whether register j holds the pair's low position.
+// One stage on the registers, compact form: the pairs (j, j + 2^I); bit j
+// of `low` tells whether register j is the pair's low position.  Six
+// instructions per pair.
 template <int I, int KEY, typename V>
 __device__ __forceinline__ void ce_regs(V (&v)[1 << kSortRegBits], uint32_t low)
 {
@@ -79,19 +80,67 @@ __device__ __forceinline__ void ce_regs(V (&v)[1 << kSortRegBits], uint32_t low)
     }
 }
 
-
-// ce_regs with I = k for a k known at compile time after unrolling.
 template <int KEY, typename V>
 __device__ __forceinline__ void ce_regs_k(int k, V (&v)[1 << kSortRegBits], uint32_t low)
 {
-    static_assert(kSortRegBits == 4, "one case per register bit");
     if (k == 0) ce_regs<0, KEY>(v, low);
     else if (k == 1) ce_regs<1, KEY>(v, low);
     else if (k == 2) ce_regs<2, KEY>(v, low);
     else ce_regs<3, KEY>(v, low);
 }
 
-template <int E_LOG, int KEY>
+// One stage on the registers with its orientation fixed at compile time:
+// the pairs (j, j + 2^K), and register j is the pair's low position (it
+// keeps the smaller key, Sec. 6.1) iff parity(j & HM) == B.  Three
+// instructions per pair: one comparison, two selects.
+template <int K, int HM, int B, int KEY, typename V>
+__device__ __forceinline__ void ce_fixed(V (&v)[1 << kSortRegBits])
+{
+#pragma unroll
+    for (int j = 0; j < (1 << kSortRegBits); ++j) {
+        if (j & (1 << K)) continue;
+        const int jj = j | (1 << K);
+        const bool low = (__popc(j & HM) & 1) == B;
+        const int lo = low ? j : jj, hi = low ? jj : j;
+        const V a = v[lo], b = v[hi];
+        const bool k = keep<KEY>(a, b);
+        v[lo] = k ? a : b;
+        v[hi] = k ? b : a;
+    }
+}
+
+// Select the variant of stage bit K for the block's (hm, b): hm has bit K
+// clear; both are the same for every thread of the block.
+template <int K, int KEY, int HM, typename V>
+__device__ __forceinline__ void ce_dispatch(V (&v)[1 << kSortRegBits], uint32_t hm, uint32_t b)
+{
+    if constexpr (HM < (1 << kSortRegBits)) {
+        if constexpr ((HM >> K) & 1) {
+            ce_dispatch<K, KEY, HM + 1>(v, hm, b);
+        } else {
+            if (hm == (uint32_t)HM) {
+                if (b) ce_fixed<K, HM, 1, KEY>(v);
+                else ce_fixed<K, HM, 0, KEY>(v);
+            } else {
+                ce_dispatch<K, KEY, HM + 1>(v, hm, b);
+            }
+        }
+    }
+}
+
+// The stage in register bit k (known at compile time after unrolling).
+template <int KEY, typename V>
+__device__ __forceinline__ void ce_stage(int k, V (&v)[1 << kSortRegBits], uint32_t hm,
+                                         uint32_t b)
+{
+    static_assert(kSortRegBits == 4, "one case per register bit");
+    if (k == 0) ce_dispatch<0, KEY, 0>(v, hm, b);
+    else if (k == 1) ce_dispatch<1, KEY, 0>(v, hm, b);
+    else if (k == 2) ce_dispatch<2, KEY, 0>(v, hm, b);
+    else ce_dispatch<3, KEY, 0>(v, hm, b);
+}
+
+template <int E_LOG, int KEY, bool UNROLLED>
 __device__ __forceinline__ void run_groups(const SortDesc &sd, uint32_t sbase, uint64_t bc)
 {
     using V = typename KeyWord<E_LOG>::type;
@@ -106,6 +155,7 @@ __device__ __forceinline__ void run_groups(const SortDesc &sd, uint32_t sbase, u
 #pragma unroll
         for (int t = 0; t < 3; ++t)
             if ((tid >> (5 + t)) & 1u) tq ^= G.warp[t];
+        // byte offsets of the registers' slots, relative to the round's base
         uint32_t roff[E];
         roff[0] = 0;
 #pragma unroll
@@ -113,7 +163,7 @@ __device__ __forceinline__ void run_groups(const SortDesc &sd, uint32_t sbase, u
             // j with its lowest set bit cleared, then that bit's vector
             int lb = 0;
             while (!((j >> lb) & 1)) ++lb;
-            roff[j] = roff[j & (j - 1)] ^ G.reg[lb];
+            roff[j] = roff[j & (j - 1)] ^ ((uint32_t)G.reg[lb] << E_LOG);
         }
         const uint32_t rounds = 1u << sd.round_bits;
         const uint32_t end = (uint32_t)G.first + G.count;
@@ -121,23 +171,28 @@ __device__ __forceinline__ void run_groups(const SortDesc &sd, uint32_t sbase, u
             uint32_t qb = tq;
             for (uint32_t t = 0; t < sd.round_bits; ++t)
                 if ((rd >> t) & 1u) qb ^= G.round[t];
+            const uint32_t qbyte = qb << E_LOG;
             V v[E];
 #pragma unroll
-            for (int j = 0; j < E; ++j) v[j] = lds_key<E_LOG>(sbase + ((qb ^ roff[j]) << E_LOG));
-            // stage first + k pairs the registers that differ in bit k
+            for (int j = 0; j < E; ++j) v[j] = lds_key<E_LOG>(sbase + (qbyte ^ roff[j]));
+            // stage first + k pairs the registers that differ in bit k; its
+            // orientation is the block's (hmask, bit of bc)
 #pragma unroll
             for (int k = 0; k < kSortRegBits; ++k) {
                 const uint32_t s = (uint32_t)G.first + (uint32_t)k;
                 if (s < end) {
                     const SortStage &st = sd.st[s];
-                    const uint32_t tpar =
-                        ((uint32_t)__popc(st.hslot & qb) ^ (uint32_t)(bc >> s)) & 1u;
-                    const uint32_t low = (uint32_t)st.jmask ^ (tpar ? 0u : 0xFFFFu);
-                    ce_regs_k<KEY>(k, v, low);
+                    const uint32_t blk = (uint32_t)(bc >> s) & 1u;
+                    if constexpr (UNROLLED) {
+                        ce_stage<KEY>(k, v, st.hmask, blk);
+                    } else {
+                        const uint32_t low0 = st.low0;
+                        ce_regs_k<KEY>(k, v, blk ? ~low0 : low0);
+                    }
                 }
             }
 #pragma unroll
-            for (int j = 0; j < E; ++j) sts_key<E_LOG>(sbase + ((qb ^ roff[j]) << E_LOG), v[j]);
+            for (int j = 0; j < E; ++j) sts_key<E_LOG>(sbase + (qbyte ^ roff[j]), v[j]);
         }
         __syncthreads();
     }
@@ -169,7 +224,7 @@ __device__ __forceinline__ uint64_t block_stage_bits(const PassDesc &d, const So
     return ((uint64_t)hi << 32) | lo;
 }
 
-template <int E_LOG, int KEY>
+template <int E_LOG, int KEY, bool UNROLLED>
 __global__ void __launch_bounds__(256)
     bmmc_sort_pass(const __grid_constant__ PassDesc d, const __grid_constant__ SortDesc sd,
                    const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
@@ -187,7 +242,7 @@ __global__ void __launch_bounds__(256)
     dev::cp_async_wait_all();
     __syncthreads();
     const uint64_t bc = block_stage_bits(d, *tab, cta);
-    run_groups<E_LOG, KEY>(*tab, sbase, bc);
+    run_groups<E_LOG, KEY, UNROLLED>(*tab, sbase, bc);
     dev::tile_store<E_LOG, dev::kKeyNone>(d, a, out, sbase);
 }
 
@@ -250,25 +305,34 @@ cudaError_t launch_pdl(void (*kernel)(Args...), dim3 grid, dim3 block, size_t sm
 constexpr int kMaxDevices = 64;
 constexpr int kSortTile = 64 * 1024;  // largest tile buffer of a fused pass
 constexpr int kSortSmem = kSortTile + (int)((sizeof(SortDesc) + 127) & ~(size_t)127);
-std::atomic<bool> g_sort_attr[kMaxDevices][2][7];
+std::atomic<bool> g_sort_attr[kMaxDevices][2][7][2];
 
-template <int E_LOG, int KEY>
-cudaError_t launch_typed(const PassDesc &d, const SortDesc &sd, const void *in, void *out,
-                         cudaStream_t s)
+template <int E_LOG, int KEY, bool UNROLLED>
+cudaError_t launch_variant(const PassDesc &d, const SortDesc &sd, const void *in, void *out,
+                           cudaStream_t s)
 {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_sort_attr[dev][E_LOG - 2][KEY].load(std::memory_order_acquire)) {
-        err = cudaFuncSetAttribute(bmmc_sort_pass<E_LOG, KEY>,
+    std::atomic<bool> &flag = g_sort_attr[dev][E_LOG - 2][KEY][UNROLLED ? 1 : 0];
+    if (!flag.load(std::memory_order_acquire)) {
+        err = cudaFuncSetAttribute(bmmc_sort_pass<E_LOG, KEY, UNROLLED>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
         if (err != cudaSuccess) return err;
-        g_sort_attr[dev][E_LOG - 2][KEY].store(true, std::memory_order_release);
+        flag.store(true, std::memory_order_release);
     }
-    return launch_pdl(bmmc_sort_pass<E_LOG, KEY>, dim3(1u << d.n_cta), dim3(256),
+    return launch_pdl(bmmc_sort_pass<E_LOG, KEY, UNROLLED>, dim3(1u << d.n_cta), dim3(256),
                       d.smem_bytes + sizeof(SortDesc), s, d, sd, static_cast<const uint8_t *>(in),
                       static_cast<uint8_t *>(out));
+}
+
+template <int E_LOG, int KEY>
+cudaError_t launch_typed(const PassDesc &d, const SortDesc &sd, const void *in, void *out,
+                         cudaStream_t s)
+{
+    return sd.unrolled ? launch_variant<E_LOG, KEY, true>(d, sd, in, out, s)
+                       : launch_variant<E_LOG, KEY, false>(d, sd, in, out, s);
 }
 
 }  // namespace

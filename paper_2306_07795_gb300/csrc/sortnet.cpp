@@ -336,9 +336,90 @@ uint64_t mix64(uint64_t *s)
     return z ^ (z >> 31);
 }
 
+// Basis of the vectors v of F2^P with parity(f & v) = 0 for every f in fs.
+std::vector<uint64_t> nullspace(const std::vector<uint64_t> &fs, int P)
+{
+    std::vector<uint64_t> rows = fs;
+    std::vector<int> pivcol;
+    size_t r = 0;
+    for (int col = 0; col < P && r < rows.size(); ++col) {
+        size_t sel = rows.size();
+        for (size_t i = r; i < rows.size(); ++i)
+            if ((rows[i] >> col) & 1ull) {
+                sel = i;
+                break;
+            }
+        if (sel == rows.size()) continue;
+        std::swap(rows[r], rows[sel]);
+        for (size_t i = 0; i < rows.size(); ++i)
+            if (i != r && ((rows[i] >> col) & 1ull)) rows[i] ^= rows[r];
+        pivcol.push_back(col);
+        ++r;
+    }
+    std::vector<uint64_t> basis;
+    for (int col = 0; col < P; ++col) {
+        bool piv = false;
+        for (int pc : pivcol) piv |= pc == col;
+        if (piv) continue;
+        uint64_t v = 1ull << col;
+        for (size_t i = 0; i < r; ++i)
+            if ((rows[i] >> col) & 1ull) v |= 1ull << pivcol[i];
+        basis.push_back(v);
+    }
+    return basis;
+}
+
+// Lanes for a group: 5 vectors of the span of `pool` whose low bank bits
+// (the 5 low slot bits for 4-byte keys, the 4 low ones of lanes 0-3 for
+// 8-byte keys) are independent, independent of `fixed` and of each other.
+// Falls back to the best rank found (bank conflicts, results still exact).
+bool pick_lanes(const std::vector<uint64_t> &pool, const std::vector<uint64_t> &fixed,
+                int e_log, uint64_t *seed, std::vector<uint64_t> *lanes)
+{
+    const int bank_lanes = e_log == 2 ? 5 : 4;
+    const uint64_t bank_mask = e_log == 2 ? 31ull : 15ull;
+    int best = -1;
+    std::vector<uint64_t> best_lanes;
+    for (int tries = 0; tries < 4096; ++tries) {
+        std::vector<uint64_t> ln;
+        std::vector<uint64_t> all = fixed;
+        for (int t = 0; t < 5; ++t) {
+            uint64_t v = 0;
+            for (int attempt = 0; attempt < 64; ++attempt) {
+                v = 0;
+                const uint64_t pick = mix64(seed);
+                for (size_t i = 0; i < pool.size(); ++i)
+                    if ((pick >> (i % 64)) & 1ull) v ^= pool[i];
+                if (v && !in_span(all, v)) break;
+                v = 0;
+            }
+            if (!v) break;
+            ln.push_back(v);
+            all.push_back(v);
+        }
+        if (ln.size() != 5) continue;
+        std::vector<uint64_t> low;
+        for (int t = 0; t < bank_lanes; ++t) low.push_back(ln[t] & bank_mask);
+        const int r = rank_of(low);
+        if (r > best) {
+            best = r;
+            best_lanes = ln;
+        }
+        if (best == bank_lanes) break;
+    }
+    if (best < 0) return false;
+    *lanes = best_lanes;
+    return true;
+}
+
 // Register groups of one pass and their thread mappings (physical slots).
+// A group takes consecutive stages while their partner vectors are
+// independent and the matrix M[a][b] = parity(hslot_a & delta_b) stays
+// invertible: then the common kernel K0 of the group's low tests is a
+// complement of the partner vectors, and the lanes, warps, rounds and unused
+// register bits are all taken from K0 (see SortStage).
 int build_groups(SortDesc *sd, const std::vector<uint32_t> &delta,
-                 const std::vector<uint32_t> &hslot, int P)
+                 const std::vector<uint32_t> &hslot, int P, int e_log)
 {
     const int R = kSortRegBits;
     const int round_bits = P - R - 8;
@@ -347,60 +428,72 @@ int build_groups(SortDesc *sd, const std::vector<uint32_t> &delta,
     const int S = (int)delta.size();
     int g = 0, s = 0;
     uint64_t seed = 0xB17C0FFEEull ^ (uint64_t)P;
+    auto m_invertible = [&](int first, int count) {
+        std::vector<uint64_t> rows;
+        for (int a = 0; a < count; ++a) {
+            uint64_t row = 0;
+            for (int b = 0; b < count; ++b)
+                row |= (uint64_t)__builtin_parity(hslot[first + a] & delta[first + b]) << b;
+            rows.push_back(row);
+        }
+        return rank_of(rows) == count;
+    };
     while (s < S) {
         if (g >= kSortMaxGroups) return -3;
         SortGroup &G = sd->grp[g];
         memset(&G, 0, sizeof(G));
         std::vector<uint64_t> reg;
         G.first = (uint16_t)s;
-        // the k-th stage of the group differs in register bit k: a stage
-        // joins while its partner vector is independent of the group's
-        while (s < S && (int)reg.size() < R && !in_span(reg, delta[s])) {
+        while (s < S && (int)reg.size() < R && !in_span(reg, delta[s]) &&
+               m_invertible(G.first, s - G.first + 1)) {
             reg.push_back(delta[s]);
             ++s;
         }
         G.count = (uint16_t)(s - G.first);
-        // complete the register vectors to R with unit vectors
-        for (int j = 0; j < P && (int)reg.size() < R; ++j)
-            if (!in_span(reg, 1ull << j)) reg.push_back(1ull << j);
-        // lanes: low bits e_0..e_4 (distinct banks for every register and
-        // round), plus high bits chosen so that lanes and registers are
-        // independent
+        std::vector<uint64_t> fs;
+        for (int q = G.first; q < s; ++q) fs.push_back(hslot[q]);
+        const std::vector<uint64_t> k0 = nullspace(fs, P);
+        // lanes from K0, then unused register bits, warps and rounds from K0
         std::vector<uint64_t> lanes;
-        bool found = false;
-        for (int tries = 0; tries < 4096 && !found; ++tries) {
-            lanes.clear();
-            for (int t = 0; t < 5; ++t) {
-                uint64_t hi = 0;
-                if (tries > 0) hi = mix64(&seed) & (((1ull << P) - 1) & ~31ull);
-                lanes.push_back((1ull << t) | hi);
-            }
-            std::vector<uint64_t> all = reg;
-            all.insert(all.end(), lanes.begin(), lanes.end());
-            found = rank_of(all) == R + 5;
-        }
-        if (!found) return -3;
+        if (!pick_lanes(k0, reg, e_log, &seed, &lanes)) return -3;
         std::vector<uint64_t> all = reg;
         all.insert(all.end(), lanes.begin(), lanes.end());
-        std::vector<uint64_t> rest;
-        for (int j = 0; j < P && (int)all.size() < P; ++j)
-            if (!in_span(all, 1ull << j)) {
-                all.push_back(1ull << j);
-                rest.push_back(1ull << j);
+        std::vector<uint64_t> fill;
+        for (uint64_t v : k0)
+            if ((int)(all.size()) < P && !in_span(all, v)) {
+                all.push_back(v);
+                fill.push_back(v);
             }
-        if ((int)all.size() != P || (int)rest.size() != 3 + round_bits) return -3;
+        if ((int)all.size() != P || (int)fill.size() != (R - (int)reg.size()) + 3 + round_bits)
+            return -3;
+        size_t fi = 0;
+        while ((int)reg.size() < R) reg.push_back(fill[fi++]);
         for (int t = 0; t < R; ++t) G.reg[t] = (uint16_t)reg[t];
         for (int t = 0; t < 5; ++t) G.lane[t] = (uint16_t)lanes[t];
-        for (int t = 0; t < 3; ++t) G.warp[t] = (uint16_t)rest[t];
-        for (int t = 0; t < round_bits; ++t) G.round[t] = (uint16_t)rest[3 + t];
-        // each stage's low test on the registers
-        uint64_t regtab[kSortRegBits];
-        for (int t = 0; t < R; ++t) regtab[t] = reg[t];
-        for (int q = G.first; q < s; ++q) {
-            uint32_t jm = 0;
+        for (int t = 0; t < 3; ++t) G.warp[t] = (uint16_t)fill[fi++];
+        for (int t = 0; t < round_bits; ++t) G.round[t] = (uint16_t)fill[fi++];
+        // each stage's orientation mask over the other register bits
+        for (int k = 0; k < G.count; ++k) {
+            const int q = G.first + k;
+            uint32_t hm = 0;
+            for (int t = 0; t < R; ++t) {
+                const uint32_t par = (uint32_t)__builtin_parityll(hslot[q] & reg[t]);
+                if (t == k) {
+                    if (!par) return -3;  // g_s . u_s = 1
+                } else {
+                    hm |= par << t;
+                }
+            }
+            // lanes, warps and rounds do not change the low test
+            for (int t = 0; t < 5; ++t)
+                if (__builtin_parityll(hslot[q] & lanes[t])) return -3;
+            for (size_t t = R - (reg.size() - (size_t)G.count); t < fill.size(); ++t)
+                if (__builtin_parityll(hslot[q] & fill[t])) return -3;
+            sd->st[q].hmask = (uint8_t)hm;
+            uint32_t low0 = 0;
             for (uint32_t j = 0; j < (1u << R); ++j)
-                jm |= (uint32_t)__builtin_parityll(hslot[q] & xor_bits64(regtab, j)) << j;
-            sd->st[q].jmask = (uint16_t)jm;
+                if (!((j >> k) & 1u) && !__builtin_parity(j & hm)) low0 |= 1u << j;
+            sd->st[q].low0 = (uint16_t)low0;
         }
         ++g;
     }
@@ -410,7 +503,7 @@ int build_groups(SortDesc *sd, const std::vector<uint32_t> &delta,
 
 }  // namespace
 
-int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2)
+int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2, int compare_code)
 {
     const int e_log = (key >= BMMC_KEY_I32 && key <= BMMC_KEY_F32) ? 2 : 3;
     const int N = n + b;
@@ -507,6 +600,13 @@ int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2)
         SortDesc sd;
         memset(&sd, 0, sizeof(sd));
         sd.key = (uint32_t)key;
+        // The unrolled orientation variants pay off on large arrays of 4-byte
+        // keys (GB300: 5 % at 2^20, 11 % at 2^22 and 2^24); smaller sorts are
+        // bound by latency, where the compact loop's smaller code fetches
+        // faster, and 8-byte keys measured faster with the compact loop at
+        // every size.
+        sd.unrolled = compare_code == 2 ||
+                      (compare_code == 0 && e_log == 2 && N >= kSortUnrolledMinBits);
         sd.n_stage = (uint32_t)(pp.end - pp.first);
         std::vector<uint32_t> delta, hslot;
         for (int s = pp.first; s < pp.end; ++s) {
@@ -526,7 +626,6 @@ int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2)
             if (!__builtin_parity(hs & dl)) return BMMC_ERR_INVALID;  // g_s . u_s = 1
             SortStage &st = sd.st[s - pp.first];
             st.hin = (uint32_t)hin;
-            st.hslot = (uint16_t)hs;
             delta.push_back(dl);
             hslot.push_back(hs);
         }
@@ -537,7 +636,7 @@ int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2)
                      << (s - pp.first);
             sd.cta_mask[bb] = m;
         }
-        rc = build_groups(&sd, delta, hslot, map.P);
+        rc = build_groups(&sd, delta, hslot, map.P, e_log);
         if (rc) return rc;
         p->pass.push_back(desc);
         p->ce.push_back(sd);
@@ -681,18 +780,17 @@ int emulate(const bmmc_sort_plan_s *p, const void *in_v, void *out_v)
                         for (uint32_t j = 0; j < E; ++j) v[j] = sm[qb ^ roff[j]];
                         for (uint32_t s = G.first; s < (uint32_t)G.first + G.count; ++s) {
                             const SortStage &st = sd.st[s];
-                            const uint32_t tpar =
-                                ((uint32_t)__builtin_parity(st.hslot & qb) ^ (uint32_t)(bc >> s)) &
-                                1u;
-                            // bit j set: register j holds the pair's low position
-                            // (its index has g_s . x = 0)
-                            const uint32_t low = st.jmask ^ (tpar ? 0u : 0xFFFFu);
+                            // register j (stage bit 0) holds the pair's low
+                            // position iff parity(j & hmask) is the block's bit
+                            const uint32_t blk = (uint32_t)(bc >> s) & 1u;
                             const uint32_t bit = 1u << (s - G.first);
                             for (uint32_t j = 0; j < E; ++j) {
                                 if (j & bit) continue;
                                 const uint32_t jj = j | bit;
-                                if ((low >> j) & 1u) order_pair(p->key, &v[j], &v[jj]);
-                                else order_pair(p->key, &v[jj], &v[j]);
+                                if ((uint32_t)__builtin_parity(j & st.hmask) == blk)
+                                    order_pair(p->key, &v[j], &v[jj]);
+                                else
+                                    order_pair(p->key, &v[jj], &v[j]);
                             }
                         }
                         for (uint32_t j = 0; j < E; ++j) sm[qb ^ roff[j]] = v[j];
@@ -749,16 +847,18 @@ int bmmc_sort_plan_create(bmmc_sort_plan *out, int n, int b, int key_type,
     *out = nullptr;
     if (n < 1 || n > 30 || b < 0 || n + b > 32) return BMMC_ERR_INVALID;
     if (key_type < BMMC_KEY_I32 || key_type > BMMC_KEY_F64) return BMMC_ERR_UNSUPPORTED;
-    int block_log2 = 0;
+    int block_log2 = 0, compare_code = 0;
     if (opts) {
         for (int r : opts->reserved)
             if (r) return BMMC_ERR_UNSUPPORTED;
         block_log2 = opts->block_log2;
+        compare_code = opts->compare_code;
+        if (compare_code < 0 || compare_code > 2) return BMMC_ERR_UNSUPPORTED;
         if (block_log2 && (block_log2 < 12 || block_log2 > 16)) return BMMC_ERR_UNSUPPORTED;
     }
     return guarded([&] {
         bmmc_sort_plan_s *p = new bmmc_sort_plan_s();
-        const int rc = sortnet::plan_sort(p, n, b, key_type, block_log2);
+        const int rc = sortnet::plan_sort(p, n, b, key_type, block_log2, compare_code);
         if (rc) {
             delete p;
             return rc;

@@ -28,7 +28,7 @@ namespace bmmc {
 namespace sortnet {
 
 // Build the plan (host only).  Returns 0 or a negative bmmc status.
-int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2);
+int plan_sort(bmmc_sort_plan_s *p, int n, int b, int key, int block_log2, int compare_code);
 
 // Run the plan's tables on the host, exactly as the kernels index them:
 // in and out hold 2^N keys.  Returns 0.

@@ -55,8 +55,8 @@ def schedule(n):
 class _SortPlan:
     """Owner of one bmmc_sort_plan handle (fused passes)."""
 
-    def __init__(self, n, b, key, block_log2):
-        self.h = B.bmmc_sort_plan_create(n, b, key, block_log2)
+    def __init__(self, n, b, key, block_log2, compare_code):
+        self.h = B.bmmc_sort_plan_create(n, b, key, block_log2, compare_code)
         self.ws_bytes = B.bmmc_sort_workspace_bytes(self.h)
         self.passes = B.bmmc_sort_plan_num_passes(self.h)
 
@@ -84,12 +84,13 @@ class SortingNetwork:
     pass per stage (bmmc_execute_ce), the straightforward form of Sec. 6.1's
     program; both give the same output bit for bit."""
 
-    def __init__(self, n, fused=True, block_log2=0):
+    def __init__(self, n, fused=True, block_log2=0, compare_code=0):
         if n < 1 or n > 30:
             raise ValueError("n must be in 1..30")
         self.n = n
         self.fused = fused
         self.block_log2 = block_log2
+        self.compare_code = compare_code
         self.stage_rows, self.final_rows, self._final_identity = schedule(n)
         self._plans = {}
 
@@ -110,7 +111,7 @@ class SortingNetwork:
     def _sort_plan(self, key, b):
         k = ("fused", key, b)
         if k not in self._plans:
-            self._plans[k] = _SortPlan(self.n, b, key, self.block_log2)
+            self._plans[k] = _SortPlan(self.n, b, key, self.block_log2, self.compare_code)
         return self._plans[k]
 
     def describe(self, dtype, rows=1):
