@@ -52,7 +52,7 @@ class Request:
 class Server:
     def __init__(self, device, mode="continuous", streams=4, budget_bytes=40 * 10**9,
                  arena_bytes=None, flags=B.BMMC_PLAN_PAPER, group_max_bytes=1 << 22,
-                 group_min=4, keep_outputs=False, plan_cache=None, large_log2=0):
+                 group_min=4, keep_outputs=False, plan_cache=None, large_log2=None):
         import torch
         self.device = torch.device(device)
         cfg = B.bmmc_server_config()
@@ -68,7 +68,12 @@ class Server:
         if plan_cache is None:
             plan_cache = 0 if mode == "plain" else 1024
         cfg.plan_cache = int(plan_cache)
-        # requests of at least 2^large_log2 bytes on a high-priority stream
+        # Requests of at least 2^large_log2 bytes (default 256 MiB arrays,
+        # whose two passes keep the GPU busy for about 0.16 ms or more) run on
+        # a high-priority stream, so that small requests arriving meanwhile
+        # take only the SMs they leave idle.  0 = every stream alike.
+        if large_log2 is None:
+            large_log2 = 28 if mode != "plain" else 0
         cfg.large_log2 = int(large_log2)
         self.mode = mode
         with torch.cuda.device(self.device):
