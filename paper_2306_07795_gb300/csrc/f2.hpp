@@ -103,11 +103,14 @@ inline bool inverse(const Mat &a, Mat *out)
         if (piv < 0) return false;
         uint64_t t = left[col]; left[col] = left[piv]; left[piv] = t;
         t = right[col]; right[col] = right[piv]; right[piv] = t;
-        for (int i = 0; i < n; ++i)
-            if (i != col && ((left[i] >> col) & 1ull)) {
-                left[i] ^= left[col];
-                right[i] ^= right[col];
-            }
+        // clear column `col` from every other row (branch-free: the rows'
+        // bits are data, and mispredicted branches dominated the time)
+        const uint64_t lc = left[col], rc = right[col];
+        for (int i = 0; i < n; ++i) {
+            const uint64_t sel = (0 - ((left[i] >> col) & 1ull)) & (i != col ? ~0ull : 0ull);
+            left[i] ^= lc & sel;
+            right[i] ^= rc & sel;
+        }
     }
     out->n = n;
     for (int i = 0; i < n; ++i) out->r[i] = right[i];
@@ -121,6 +124,44 @@ inline Mat reverse(int n)
     m.n = n;
     for (int i = 0; i < n; ++i) m.r[i] = 1ull << (n - 1 - i);
     return m;
+}
+
+// The low n bits of x in reverse order (bit i moves to bit n - 1 - i).
+inline uint64_t reverse_bits(uint64_t x, int n)
+{
+    x = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+    x = ((x >> 2) & 0x3333333333333333ull) | ((x & 0x3333333333333333ull) << 2);
+    x = ((x >> 4) & 0x0f0f0f0f0f0f0f0full) | ((x & 0x0f0f0f0f0f0f0f0full) << 4);
+    x = ((x >> 8) & 0x00ff00ff00ff00ffull) | ((x & 0x00ff00ff00ff00ffull) << 8);
+    x = ((x >> 16) & 0x0000ffff0000ffffull) | ((x & 0x0000ffff0000ffffull) << 16);
+    x = (x >> 32) | (x << 32);
+    return n ? x >> (64 - n) : 0;
+}
+
+// R A R (R the bit-reverse matrix): row i is row n - 1 - i of A with its
+// columns reversed.  Equal to mul(mul(reverse(n), a), reverse(n)).
+inline Mat reverse_both(const Mat &a)
+{
+    Mat out;
+    out.n = a.n;
+    for (int i = 0; i < a.n; ++i) out.r[i] = reverse_bits(a.r[a.n - 1 - i], a.n);
+    return out;
+}
+
+// A P for a permutation matrix P (one set bit per row): column j of A moves
+// to the column of P's row j.  Equal to mul(a, p).
+inline Mat mul_perm(const Mat &a, const Mat &p)
+{
+    int to[64];
+    for (int j = 0; j < p.n; ++j) to[j] = __builtin_ctzll(p.r[j]);
+    Mat out;
+    out.n = a.n;
+    for (int i = 0; i < a.n; ++i) {
+        uint64_t acc = 0;
+        for (int j = 0; j < p.n; ++j) acc |= ((a.r[i] >> j) & 1ull) << to[j];
+        out.r[i] = acc;
+    }
+    return out;
 }
 
 // Zero columns of the rows [k, n): the columns j with a_ij = 0 for all i >= k.
@@ -150,8 +191,7 @@ inline uint64_t tiled_columns(const Mat &a, int k)
 inline bool ulp(const Mat &a, Mat *u, Mat *l, Mat *p)
 {
     int n = a.n;
-    Mat r = reverse(n);
-    Mat w = mul(mul(r, a), r);
+    Mat w = reverse_both(a);
     Mat lp = Mat::identity(n);
     int perm[64];
     for (int i = 0; i < n; ++i) perm[i] = i;
@@ -159,26 +199,27 @@ inline bool ulp(const Mat &a, Mat *u, Mat *l, Mat *p)
         uint64_t cand = w.r[i] >> i;
         if (!cand) return false;
         int j = i + __builtin_ctzll(cand);
-        if (j != i) {
+        if (j != i) {  // swap columns i and j
             uint64_t m = (1ull << i) | (1ull << j);
             for (int t = 0; t < n; ++t) {
-                uint64_t bi = (w.r[t] >> i) & 1ull, bj = (w.r[t] >> j) & 1ull;
-                if (bi != bj) w.r[t] ^= m;
+                uint64_t diff = ((w.r[t] >> i) ^ (w.r[t] >> j)) & 1ull;
+                w.r[t] ^= m & (0 - diff);
             }
             int tmp = perm[i]; perm[i] = perm[j]; perm[j] = tmp;
         }
-        for (int t = i + 1; t < n; ++t)
-            if ((w.r[t] >> i) & 1ull) {
-                w.r[t] ^= w.r[i];
-                lp.r[t] |= 1ull << i;
-            }
+        const uint64_t wi = w.r[i];
+        for (int t = i + 1; t < n; ++t) {  // branch-free elimination
+            const uint64_t bit = (w.r[t] >> i) & 1ull;
+            w.r[t] ^= wi & (0 - bit);
+            lp.r[t] |= bit << i;
+        }
     }
     Mat pp;
     pp.n = n;
     for (int i = 0; i < n; ++i) pp.r[i] = 1ull << perm[i];
-    *u = mul(mul(r, lp), r);
-    *l = mul(mul(r, w), r);
-    *p = mul(mul(r, pp), r);
+    *u = reverse_both(lp);
+    *l = reverse_both(w);
+    *p = reverse_both(pp);
     return true;
 }
 
@@ -188,9 +229,10 @@ inline bool tiled_factors(const Mat &a, Mat *t1, Mat *t2)
 {
     Mat u, l, p;
     if (!ulp(a, &u, &l, &p)) return false;
-    Mat r = reverse(a.n);
-    *t1 = mul(u, r);
-    *t2 = mul(mul(r, l), p);
+    // U R reverses the columns of U; R L reverses the rows of L
+    t1->n = a.n;
+    for (int i = 0; i < a.n; ++i) t1->r[i] = reverse_bits(u.r[i], a.n);
+    *t2 = mul_perm(mul(reverse(a.n), l), p);
     return true;
 }
 

@@ -172,8 +172,7 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
     for (int j = 0; j < k; ++j) kappa[j] = tinv.col(j);
     auto B = [&](uint64_t ylow) {
         uint64_t v = 0;
-        for (int j = 0; j < k; ++j)
-            if ((ylow >> j) & 1ull) v ^= kappa[j];
+        for (int j = 0; j < k; ++j) v ^= kappa[j] & (0 - ((ylow >> j) & 1ull));
         return v;
     };
 
@@ -219,11 +218,11 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
     auto Phi = [&](uint64_t v) -> uint32_t {
         uint32_t r = 0;
         uint64_t h = v & ~lowmask;
-        for (int j = 0; j < m; ++j)
-            if ((v >> piv[j]) & 1ull) {
-                r |= 1u << j;
-                h ^= rowv[j];
-            }
+        for (int j = 0; j < m; ++j) {
+            const uint64_t bit = (v >> piv[j]) & 1ull;
+            r |= (uint32_t)bit << j;
+            h ^= rowv[j] & (0 - bit);
+        }
         if (h) phi_ok = false;
         return (r << k) | (uint32_t)(v & lowmask);
     };
