@@ -6,10 +6,13 @@
  * one-pass plan, (R L P, 0) for a two-pass plan) run as one launch per
  * element size present; all second passes ((U R, c)) run as a second such
  * launch.  Each launch is a persistent grid of (SMs x resident blocks) thread
- * blocks that walk contiguous ranges of the batch's tiles, so many small
+ * blocks that take chunks of consecutive tiles of the batch, so many small
  * arrays, which cannot fill the GPU one at a time (Sec. 6, arrays under 2^20
  * elements), share the machine, and a batch of any size costs at most six
- * launches.  The launches only read tables uploaded at creation.
+ * launches.  The launches read the tables uploaded at creation and update
+ * two chunk counters per launch in the same memory (each launch leaves them
+ * at zero when it ends), so the launches of one batch must not overlap one
+ * another (they write the same outputs anyway).
  *
  * Conventions are those of bmmc.h: device buffers of 2^n * elem_bytes bytes,
  * 16-byte aligned, caller-owned.
@@ -31,7 +34,8 @@ typedef struct bmmc_batch_s *bmmc_batch;
 size_t bmmc_batch_workspace_bytes(const bmmc_plan *plans, int count);
 
 /* Device bytes of a batch's tables (bmmc_batch_create's `table`): about
- * 1.8 KB per pass plus 32 bytes per pass.  0 for invalid arguments. */
+ * 1.8 KB per pass plus 32 bytes per pass, plus 96 bytes of counters.  0 for
+ * invalid arguments. */
 size_t bmmc_batch_table_bytes(const bmmc_plan *plans, int count);
 
 /*

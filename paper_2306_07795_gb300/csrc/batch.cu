@@ -52,35 +52,29 @@ constexpr uint32_t kThreads = 256;
 // groups).  With three slots the loads issued for item i + 2 go to the buffer
 // item i - 1 used, which every thread finished reading before the barrier of
 // item i, so one barrier per item suffices; two slots need a second barrier
-// after the stores.  The last 16 bytes record which table each slot holds.
+// after the stores.  The last 32 bytes record which table each slot holds
+// and the chunks a block has claimed ahead.
 constexpr uint32_t kMaxSlots = 3;
 template <int E_LOG>
 __global__ void __launch_bounds__(kThreads, 4)
     bmmc_batch_pass(const BatchEntry *__restrict__ ent, uint32_t count, uint32_t total,
                     const uint8_t *__restrict__ descs, uint32_t tile_bytes, uint32_t slots,
-                    uint32_t chunk)
+                    uint32_t chunk, uint32_t *__restrict__ ctr)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t tid = threadIdx.x;
 
-    // The items are cut into chunks of `chunk` consecutive items; block b
-    // takes chunks b, b + G, b + 2G, ... (G blocks).  A chunk of ceil(total /
-    // G) items gives each block one contiguous range.
+    // The items are cut into chunks of `chunk` consecutive items.  Block b
+    // starts with chunk b; the chunks after the first G (G blocks) are
+    // claimed from a counter as blocks finish theirs, so a block slowed down
+    // by its neighbours takes fewer of them and the launch ends evenly.
+    // Blocks running at the same time still take nearby chunks.  ctr[0]
+    // counts claims and ctr[1] finished blocks; the last block to finish
+    // resets both, so the next launch of the batch starts from zero.
+    const uint32_t G = gridDim.x;
     uint32_t cid = blockIdx.x;
-    if ((uint64_t)cid * chunk >= total) return;
-    const uint32_t begin = cid * chunk;
-    uint32_t cend = total - begin > chunk ? begin + chunk : total;
-    // the item after `it` for this block (total when there is none); moves
-    // *c and *e to the next chunk when `it` ends the current one
-    auto advance = [&](uint32_t it, uint32_t *c, uint32_t *e) -> uint32_t {
-        if (it + 1 < *e) return it + 1;
-        const uint64_t start = (uint64_t)(*c + gridDim.x) * chunk;
-        if (start >= total) return total;
-        *c += gridDim.x;
-        *e = total - (uint32_t)start > chunk ? (uint32_t)start + chunk : total;
-        return (uint32_t)start;
-    };
+    uint32_t cend = 0;
     // Launched with programmatic stream serialization (phase 2 is scheduled
     // while phase 1 drains); nothing above touched global memory.
     dev::grid_dependency_wait();
@@ -89,8 +83,49 @@ __global__ void __launch_bounds__(kThreads, 4)
     // Every thread writes the same value; it is read only after a barrier.
     volatile uint32_t *held =
         reinterpret_cast<volatile uint32_t *>(smem + slots * (kDescSlot + tile_bytes));
+    // Chunks claimed ahead: chunk j of this block (j >= 1) is ring[j % 3],
+    // written by thread 0 at least one barrier before any thread reads it.
+    volatile uint32_t *ring = held + 4;
     if (tid < kMaxSlots) held[tid] = 0xffffffffu;
+    if (tid == 0) {
+        const uint32_t c0 = atomicAdd(&ctr[0], 2u);
+        ring[1] = G + c0;
+        ring[2] = G + c0 + 1;
+    }
+    auto block_done = [&]() {
+        if (tid == 0) {
+            __threadfence();  // this block's claims come before its count
+            if (atomicAdd(&ctr[1], 1u) == G - 1) {
+                ctr[0] = 0;
+                ctr[1] = 0;
+            }
+        }
+    };
     __syncthreads();
+    if ((uint64_t)cid * chunk >= total) {
+        block_done();
+        return;
+    }
+    const uint32_t begin = cid * chunk;
+    cend = total - begin > chunk ? begin + chunk : total;
+    uint32_t seq = 0;             // this block's chunks so far, minus one
+    uint32_t pending = 0;         // thread 0: a claim not yet in the ring
+    int pending_slot = -1;
+    // the item after `it` for this block (total when there is none); moves to
+    // the next claimed chunk when `it` ends the current one
+    auto advance = [&](uint32_t it) -> uint32_t {
+        if (it + 1 < cend) return it + 1;
+        ++seq;
+        cid = ring[seq % 3];
+        if (tid == 0) {  // the chunk after the next two; stored next turn
+            pending = atomicAdd(&ctr[0], 1u);
+            pending_slot = (int)((seq + 2) % 3);
+        }
+        const uint64_t start = (uint64_t)cid * chunk;
+        if (start >= total) return total;
+        cend = total - (uint32_t)start > chunk ? (uint32_t)start + chunk : total;
+        return (uint32_t)start;
+    };
 
     // Advance *a to the last entry whose first item is <= item, by doubling
     // steps and then bisection: O(log skipped) dependent loads, one for the
@@ -157,7 +192,11 @@ __global__ void __launch_bounds__(kThreads, 4)
     for (uint32_t item = begin; item < total;) {
         const int next = slot + 1 == (int)slots ? 0 : slot + 1;
         uint32_t a_next = a_cur;
-        const uint32_t nxt = advance(item, &cid, &cend);
+        if (pending_slot >= 0) {  // thread 0 only; a barrier has passed
+            ring[pending_slot] = G + pending;
+            pending_slot = -1;
+        }
+        const uint32_t nxt = advance(item);
         if (nxt < total) {
             stage(nxt, next, &a_next);
             issue(nxt, a_next, next);
@@ -178,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         slot = next;
         item = nxt;
     }
+    block_done();
 }
 
 struct Group {
@@ -186,6 +226,7 @@ struct Group {
     uint32_t count = 0;
     uint64_t total = 0;
     size_t entry_offset = 0;  // byte offset of its entries in the device block
+    size_t ctr_offset = 0;    // byte offset of its two chunk counters
     uint32_t smem = 0;
     uint32_t tile_bytes = 0;  // largest tile buffer of the group's passes
     uint32_t slots = 0;       // tile buffers (3, or 2 when 3 do not fit)
@@ -195,7 +236,7 @@ struct Group {
 };
 
 template <int E_LOG>
-cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
+cudaError_t launch_group(const Group &g, uint8_t *dmem, cudaStream_t s)
 {
     const BatchEntry *ent = reinterpret_cast<const BatchEntry *>(dmem + g.entry_offset);
     cudaLaunchConfig_t cfg = {};
@@ -210,13 +251,13 @@ cudaError_t launch_group(const Group &g, const uint8_t *dmem, cudaStream_t s)
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, bmmc_batch_pass<E_LOG>, ent, g.count, (uint32_t)g.total,
                               static_cast<const uint8_t *>(dmem), g.tile_bytes, g.slots,
-                              g.chunk);
+                              g.chunk, reinterpret_cast<uint32_t *>(dmem + g.ctr_offset));
 }
 
 // Shared memory of a group with `slots` tile buffers.
 uint32_t group_smem(uint32_t slots, uint32_t tile_bytes)
 {
-    return slots * (kDescSlot + tile_bytes) + 16;
+    return slots * (kDescSlot + tile_bytes) + 32;
 }
 
 // Three tile buffers if they fit in a block's shared memory, else two;
@@ -294,14 +335,18 @@ struct bmmc_batch_s {
 
 namespace {
 
+// At most one launch group per (phase, element size).
+constexpr int kMaxGroups = 6;
+constexpr size_t kCounterBytes = 16;  // per group: claims, finished blocks
+
 // Bytes of the device tables of a batch: one 128-byte slot per pass, then
-// one BatchEntry per (array, pass).
+// one BatchEntry per (array, pass), then the chunk counters of each group.
 size_t table_bytes(const bmmc_plan *plans, int count)
 {
     size_t passes = 0;
     for (int i = 0; i < count; ++i)
         if (plans[i]) passes += (size_t)plans[i]->npass;
-    return passes * kDescSlot + passes * sizeof(BatchEntry);
+    return passes * kDescSlot + passes * sizeof(BatchEntry) + kMaxGroups * kCounterBytes;
 }
 
 int batch_create_impl(bmmc_batch *out, const bmmc_plan *plans, int count,
@@ -418,7 +463,7 @@ int batch_create_impl(bmmc_batch *out, const bmmc_plan *plans, int count,
     uint64_t off = 0;
     for (int i = 0; i < count; ++i) {
         const bmmc_plan p = plans[i];
-        if (!p || !ins[i] || !outs[i]) return BMMC_ERR_INVALID;
+        if (!p || !ins[i] || !outs[i] || p->derived < p->npass) return BMMC_ERR_INVALID;
         if (((uintptr_t)ins[i] | (uintptr_t)outs[i]) & 15u) return BMMC_ERR_ALIGN;
         const uint64_t b = p->bytes();
         ranges.push_back({(uintptr_t)ins[i], (uintptr_t)ins[i] + b, false});
@@ -514,7 +559,8 @@ int batch_create_impl(bmmc_batch *out, const bmmc_plan *plans, int count,
     // One device block: pass tables, then the entries of every group.
     const size_t desc_bytes = (size_t)ndesc * kDescSlot;
     const size_t ent_bytes = entries.size() * sizeof(BatchEntry);
-    std::vector<uint8_t> host(desc_bytes + ent_bytes, 0);
+    // the counters start at zero (uploaded with the tables)
+    std::vector<uint8_t> host(desc_bytes + ent_bytes + groups.size() * kCounterBytes, 0);
     for (int i = 0; i < count; ++i) {
         memcpy(host.data() + (size_t)desc0[i] * kDescSlot, &plans[i]->desc[0], sizeof(PassDesc));
         if (plans[i]->npass == 2)
@@ -522,7 +568,10 @@ int batch_create_impl(bmmc_batch *out, const bmmc_plan *plans, int count,
                    sizeof(PassDesc));
     }
     memcpy(host.data() + desc_bytes, entries.data(), ent_bytes);
-    for (Group &g : groups) g.entry_offset += desc_bytes;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        groups[gi].entry_offset += desc_bytes;
+        groups[gi].ctr_offset = desc_bytes + ent_bytes + gi * kCounterBytes;
+    }
 
     bmmc_batch_s *b = new (std::nothrow) bmmc_batch_s();
     if (!b) return BMMC_ERR_OOM;
