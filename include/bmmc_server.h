@@ -5,8 +5,9 @@
  * thread and served on the current device.  Two modes:
  *
  *  BMMC_SERVER_CONTINUOUS  A scheduler thread admits each submitted request
- *      (planned in the submitting thread) as soon as its device bytes fit in
- *      the HBM budget, and launches it on the least-loaded of S streams, so
+ *      (planned in the submitting thread: the first pass only; the tables of
+ *      a second pass are derived right after the first pass is launched,
+ *      while it runs) as soon as its device bytes fit in the HBM budget, and launches it on the least-loaded of S streams, so
  *      that requests that arrive while others run start at once and overlap
  *      with them on the device.  Small requests that are admitted together
  *      are grouped into one persistent batch launch (bmmc_batch.h).  A request
@@ -53,13 +54,16 @@ typedef struct bmmc_server_config {
                                  same (n, A, c, elem_bytes); 0 = plan every
                                  request anew.  Entries in use are pinned; the
                                  least recently used free one is evicted */
-    int large_log2;           /* CONTINUOUS with S >= 2: requests whose array
-                                 holds at least 2^large_log2 bytes run on
-                                 stream 0, created with the highest priority;
-                                 the others spread over streams 1..S-1.  Small
-                                 requests that arrive while a large one runs
-                                 then fill only the SMs it leaves idle instead
-                                 of slowing it.  0 = every stream alike */
+    int large_log2;           /* CONTINUOUS with S >= 2: a request whose array
+                                 holds at least 2^large_log2 bytes and that is
+                                 launched while at most one other launch is in
+                                 flight runs on stream 0, created with the
+                                 highest priority; every other request goes to
+                                 streams 1..S-1.  Small requests that arrive
+                                 while such a large one runs fill only the SMs
+                                 it leaves idle instead of slowing it; under
+                                 load no request is favoured.  0 = every
+                                 stream alike */
     int reserved[4];          /* must be zero */
 } bmmc_server_config;
 
@@ -83,7 +87,8 @@ int bmmc_server_create(bmmc_server *out, const bmmc_server_config *cfg);
  * PLAIN: returns after planning and launching.  Errors found at submission
  * (INVALID, SINGULAR, UNSUPPORTED, TOO_LARGE for a request whose output and
  * workspace can never fit the arena) are returned here and the request is
- * not queued. */
+ * not queued.  In CONTINUOUS mode a second pass is planned at launch; a
+ * planning error there becomes the request's result status. */
 int bmmc_server_submit(bmmc_server s, uint64_t id, int n, const uint64_t *A_rows,
                        uint64_t c, size_t elem_bytes, const void *in);
 

@@ -45,8 +45,24 @@ bool overlap(const void *a, const void *b, uint64_t bytes)
     return x < y + bytes && y < x + bytes;
 }
 
+// Derive the launch tables of pass i of p.
+int derive_one(bmmc_plan_s *p, int i)
+{
+    int rc = derive_pass(p->t[i], p->tc[i], p->n, p->e_log, p->opt, &p->desc[i], &p->info[i]);
+    if (rc == 0 && p->opt.swizzle128 && !p->desc[i].tma) {
+        // the fixed swizzle did not give conflict-free gathers: this pass
+        // keeps the searched swizzle and 16-byte copies
+        PlanOptions o2 = p->opt;
+        o2.swizzle128 = false;
+        rc = derive_pass(p->t[i], p->tc[i], p->n, p->e_log, o2, &p->desc[i], &p->info[i]);
+    }
+    return rc;
+}
+
+// derive_passes: how many passes get their tables now (the rest later, by
+// plan_derive_rest).
 int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
-                size_t elem_bytes, const bmmc_plan_options *opts)
+                size_t elem_bytes, const bmmc_plan_options *opts, int derive_passes = 2)
 {
     if (!out) return BMMC_ERR_INVALID;
     *out = nullptr;
@@ -114,19 +130,13 @@ int create_impl(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
         p->t[1] = t1;  // then (U R, c)
         p->tc[1] = c;
     }
-    for (int i = 0; i < p->npass; ++i) {
-        int rc = derive_pass(p->t[i], p->tc[i], n, e_log, opt, &p->desc[i], &p->info[i]);
-        if (rc == 0 && opt.swizzle128 && !p->desc[i].tma) {
-            // the fixed swizzle did not give conflict-free gathers: this pass
-            // keeps the searched swizzle and 16-byte copies
-            PlanOptions o2 = opt;
-            o2.swizzle128 = false;
-            rc = derive_pass(p->t[i], p->tc[i], n, e_log, o2, &p->desc[i], &p->info[i]);
-        }
+    for (int i = 0; i < p->npass && i < derive_passes; ++i) {
+        int rc = derive_one(p, i);
         if (rc) {
             delete p;
             return rc;
         }
+        p->derived = i + 1;
     }
     *out = p;
     return BMMC_OK;
@@ -137,6 +147,7 @@ int execute_impl(bmmc_plan p, const void *in, void *out, void *ws, cudaStream_t 
                  int key = 0)
 {
     const uint64_t bytes = array_bytes(p);
+    if (p->derived < p->npass) return BMMC_ERR_INVALID;
     if (((uintptr_t)in | (uintptr_t)out) & 15u) return BMMC_ERR_ALIGN;
     if (overlap(in, out, bytes)) return BMMC_ERR_ALIAS;
     if (p->npass == 1) {
@@ -159,6 +170,39 @@ int verify_impl(bmmc_plan p, uint64_t max_ctas);
 int describe_impl(bmmc_plan p, char *buf, size_t len);
 
 }  // namespace
+
+namespace bmmc {
+
+int plan_create_first_pass(bmmc_plan *out, int n, const uint64_t *rows, uint64_t c,
+                           size_t elem_bytes, const bmmc_plan_options *opts)
+{
+    return guarded([&] { return create_impl(out, n, rows, c, elem_bytes, opts, 1); });
+}
+
+int plan_derive_rest(bmmc_plan p)
+{
+    if (!p) return BMMC_ERR_INVALID;
+    return guarded([&] {
+        for (int i = p->derived; i < p->npass; ++i) {
+            const int rc = derive_one(p, i);
+            if (rc) return rc;
+            p->derived = i + 1;
+        }
+        return (int)BMMC_OK;
+    });
+}
+
+int plan_launch_pass(bmmc_plan p, int pass, const void *in, void *out, bmmc_stream_t s)
+{
+    if (!p || !in || !out || pass < 0 || pass >= p->derived) return BMMC_ERR_INVALID;
+    if (((uintptr_t)in | (uintptr_t)out) & 15u) return BMMC_ERR_ALIGN;
+    if (overlap(in, out, array_bytes(p))) return BMMC_ERR_ALIAS;
+    if (debug_fail_launch()) return BMMC_ERR_CUDA;
+    return launch_pass(p->desc[pass], in, out, (cudaStream_t)s, 0) == cudaSuccess ? BMMC_OK
+                                                                         : BMMC_ERR_CUDA;
+}
+
+}  // namespace bmmc
 
 extern "C" {
 
@@ -369,7 +413,7 @@ namespace {
 
 int verify_impl(bmmc_plan p, uint64_t max_ctas)
 {
-    if (!p) return BMMC_ERR_INVALID;
+    if (!p || p->derived < p->npass) return BMMC_ERR_INVALID;
     for (int i = 0; i < p->npass; ++i) {
         std::string why;
         if (verify_pass(p->desc[i], p->t[i], p->tc[i], max_ctas, &why) != 0) {
@@ -394,7 +438,7 @@ int verify_impl(bmmc_plan p, uint64_t max_ctas)
 
 int describe_impl(bmmc_plan p, char *buf, size_t len)
 {
-    if (!p) return BMMC_ERR_INVALID;
+    if (!p || p->derived < p->npass) return BMMC_ERR_INVALID;
     std::string s = "{\"n\": " + std::to_string(p->n) +
                     ", \"elem_bytes\": " + std::to_string(1 << p->e_log) +
                     ", \"strategy\": \"" +

@@ -1,8 +1,10 @@
 // server.cpp -- native request server (include/bmmc_server.h).
 //
 // Submission plans the request in the caller's thread (bmmc_plan_create_ex),
-// so planning cost scales with the number of submitting threads.  In
-// CONTINUOUS mode a scheduler thread then admits requests in submission order
+// so planning cost scales with the number of submitting threads; in
+// CONTINUOUS mode only the first pass is planned then, and the second pass of
+// a two-pass plan is derived right after the first pass is launched, while it
+// runs.  In CONTINUOUS mode a scheduler thread then admits requests in submission order
 // while their input + output + workspace bytes fit the budget and their output
 // and workspace fit the arena, launches each on the least-loaded stream (small
 // ones admitted together share one batch launch), and retires launches as
@@ -33,6 +35,7 @@
 #include "bmmc.h"
 #include "bmmc_batch.h"
 #include "bmmc_server.h"
+#include "plan_internal.hpp"
 #include "debug_hooks.hpp"
 
 namespace {
@@ -281,12 +284,17 @@ int least_loaded(bmmc_server_s *s)
     return best;
 }
 
-// The stream a request runs on: with large_log2 set, large requests on the
-// high-priority stream 0 and the others on the least loaded of the rest.
+// The stream a request runs on.  With large_log2 set, a large request that
+// is launched while at most one other launch is in flight (the server is
+// nearly idle) runs on the high-priority stream 0, so that small requests
+// arriving meanwhile fill only the SMs it leaves idle instead of slowing it;
+// under load every request goes to the least loaded of streams 1..S-1, as a
+// large request on the priority stream would then hold back the many small
+// ones queued behind it.
 int stream_for(bmmc_server_s *s, const Req *r)
 {
     if (s->cfg.large_log2 <= 0 || s->nstreams < 2) return least_loaded(s);
-    if (r->array_bytes >= ((size_t)1 << s->cfg.large_log2)) return 0;
+    if (r->array_bytes >= ((size_t)1 << s->cfg.large_log2) && s->n_inflight <= 1) return 0;
     int best = 1;
     for (int i = 2; i < s->nstreams; ++i)
         if (s->inflight[i].size() < s->inflight[best].size()) best = i;
@@ -299,6 +307,11 @@ void note_peaks(bmmc_server_s *s)
     s->peak_inflight = std::max<uint64_t>(s->peak_inflight, s->n_inflight);
 }
 
+// Derive the tables a request's plan still lacks (sched_mu held: every
+// launch, and so every completion of a plan, even a cached one shared by
+// several requests, happens under it).
+int complete_plan(bmmc_server_s *, Req *r) { return bmmc::plan_derive_rest(r->plan); }
+
 // Launch one request on stream si (sched_mu held, buffers allocated).  A
 // request that fails to launch still completes, with its error status, once
 // the stream reaches its event.
@@ -306,7 +319,16 @@ void launch_single(bmmc_server_s *s, Req *r, int si)
 {
     Launch L;
     L.ev = take_event(s);
-    int rc = bmmc_execute_ws(r->plan, r->in, r->out, r->ws, (bmmc_stream_t)s->streams[si]);
+    const bmmc_stream_t st = (bmmc_stream_t)s->streams[si];
+    int rc;
+    if (r->plan->derived < r->plan->npass) {
+        // The first pass runs while the host derives the second pass's tables.
+        rc = bmmc::plan_launch_pass(r->plan, 0, r->in, r->ws, st);
+        if (rc == BMMC_OK) rc = complete_plan(s, r);
+        if (rc == BMMC_OK) rc = bmmc::plan_launch_pass(r->plan, 1, r->ws, r->out, st);
+    } else {
+        rc = bmmc_execute_ws(r->plan, r->in, r->out, r->ws, st);
+    }
     if (rc != BMMC_OK) r->status = rc;
     if (!L.ev || cudaEventRecord(L.ev, s->streams[si]) != cudaSuccess) {
         // no event: wait here so that completion is known
@@ -328,6 +350,8 @@ bool launch_group(bmmc_server_s *s, std::vector<Req *> &g, int si)
     std::vector<bmmc_plan> plans;
     std::vector<const void *> ins;
     std::vector<void *> outs;
+    for (Req *r : g)  // a batch takes complete plans only
+        if (complete_plan(s, r) != BMMC_OK) return false;
     for (Req *r : g) {
         plans.push_back(r->plan);
         ins.push_back(r->in);
@@ -553,7 +577,11 @@ int prepare(bmmc_server_s *s, Req *r, int n, const uint64_t *rows, uint64_t c, s
         memset(&o, 0, sizeof(o));
         o.flags = s->cfg.plan_flags;
         bmmc_plan p = nullptr;
-        int rc = bmmc_plan_create_ex(&p, n, rows, c, e, &o);
+        // Continuous mode plans the first pass only: the second pass's tables
+        // are derived at launch, while the first pass runs.
+        const bool staged = s->cfg.mode == BMMC_SERVER_CONTINUOUS;
+        int rc = staged ? bmmc::plan_create_first_pass(&p, n, rows, c, e, &o)
+                        : bmmc_plan_create_ex(&p, n, rows, c, e, &o);
         if (rc != BMMC_OK) return rc;
         r->plan = p;
         if (use_cache) {

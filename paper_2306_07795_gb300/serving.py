@@ -69,9 +69,10 @@ class Server:
             plan_cache = 0 if mode == "plain" else 1024
         cfg.plan_cache = int(plan_cache)
         # Requests of at least 2^large_log2 bytes (default 256 MiB arrays,
-        # whose two passes keep the GPU busy for about 0.16 ms or more) run on
-        # a high-priority stream, so that small requests arriving meanwhile
-        # take only the SMs they leave idle.  0 = every stream alike.
+        # whose two passes keep the GPU busy for about 0.16 ms or more) that
+        # find the server nearly idle run on a high-priority stream, so that
+        # small requests arriving meanwhile take only the SMs they leave idle.
+        # 0 = every stream alike.
         if large_log2 is None:
             large_log2 = 28 if mode != "plain" else 0
         cfg.large_log2 = int(large_log2)

@@ -267,9 +267,9 @@ def test_serving_config_full_size():
 
 
 def test_large_requests_on_priority_stream():
-    """With large_log2 set, requests of at least that many bytes run on the
-    high-priority stream 0 and the rest on streams 1..S-1; every result is
-    the same as alone."""
+    """With large_log2 set, requests of at least that many bytes that find
+    the server nearly idle run on the high-priority stream 0 and the rest on
+    streams 1..S-1; every result is the same as alone."""
     import torch
     reqs = _requests(120, rate=20000.0, n_lo=12, n_hi=22, seed=17)
     srv = serving.Server("cuda", streams=4, budget_bytes=1 << 30, arena_bytes=4 << 30,
