@@ -276,6 +276,10 @@ bool retire(bmmc_server_s *s)
     return any;
 }
 
+// Launches in flight up to which a new request follows a large one on the
+// priority stream (see stream_for).
+constexpr uint64_t kFollowMax = 3;
+
 int least_loaded(bmmc_server_s *s)
 {
     int best = 0;
@@ -286,15 +290,17 @@ int least_loaded(bmmc_server_s *s)
 
 // The stream a request runs on.  With large_log2 set, a large request that
 // is launched while at most one other launch is in flight (the server is
-// nearly idle) runs on the high-priority stream 0, so that small requests
-// arriving meanwhile fill only the SMs it leaves idle instead of slowing it;
-// under load every request goes to the least loaded of streams 1..S-1, as a
-// large request on the priority stream would then hold back the many small
-// ones queued behind it.
+// nearly idle) runs on the high-priority stream 0, and requests that arrive
+// while it runs, as long as few are in flight, queue behind it on that
+// stream, as they would in the plain loop, instead of taking SMs and
+// bandwidth from it.  Under load every request goes to the least loaded of
+// streams 1..S-1: a large request on the priority stream would then hold back
+// the many small ones queued behind it.
 int stream_for(bmmc_server_s *s, const Req *r)
 {
     if (s->cfg.large_log2 <= 0 || s->nstreams < 2) return least_loaded(s);
     if (r->array_bytes >= ((size_t)1 << s->cfg.large_log2) && s->n_inflight <= 1) return 0;
+    if (!s->inflight[0].empty() && s->n_inflight <= kFollowMax) return 0;
     int best = 1;
     for (int i = 2; i < s->nstreams; ++i)
         if (s->inflight[i].size() < s->inflight[best].size()) best = i;
