@@ -72,8 +72,9 @@ int bmmc_batch_execute(bmmc_batch b, bmmc_stream_t stream);
 /* Number of kernel launches one bmmc_batch_execute makes (1..6). */
 int bmmc_batch_num_launches(bmmc_batch b);
 
-/* One-line JSON: per launch its phase, element size, arrays, tiles, grid,
- * threads and shared memory, and the batch's total 2 * N * e bytes.
+/* One-line JSON: per launch its phase, element size, arrays, tiles
+ * ("items"), grid, items per chunk, threads and shared memory, and the
+ * batch's total 2 * N * e bytes.
  * Returns the full length needed, or a negative code. */
 int bmmc_batch_describe(bmmc_batch b, char *buf, size_t len);
 

@@ -600,9 +600,9 @@ int batch_describe_impl(bmmc_batch b, char *buf, size_t len)
         char tmp[256];
         snprintf(tmp, sizeof(tmp),
                  "%s{\"phase\": %d, \"elem_bytes\": %d, \"arrays\": %u, \"items\": %llu, "
-                 "\"grid\": %u, \"threads\": %u, \"smem_bytes\": %u}",
+                 "\"grid\": %u, \"chunk\": %u, \"threads\": %u, \"smem_bytes\": %u}",
                  i ? ", " : "", g.phase + 1, 1 << g.e_log, g.arrays,
-                 (unsigned long long)g.total, g.grid, kThreads, g.smem);
+                 (unsigned long long)g.total, g.grid, g.chunk, kThreads, g.smem);
         s += tmp;
     }
     char tail[64];

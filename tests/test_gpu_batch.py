@@ -99,6 +99,25 @@ def test_graph_replay():
     _check(outs, host)
 
 
+def test_repeated_executions_claim_chunks():
+    """Enough tiles that blocks claim chunks from the batch's counter: every
+    execution (the counter is reset by the last block of the one before)
+    writes every output again."""
+    import torch
+    ns = [24, 24, 23, 24, 22]
+    es = [4, 4, 8, 4, 16]
+    plans, ins, outs, host = _build(ns, es, bm.BMMC_PLAN_PAPER, seed0=90)
+    b = Batch(plans, ins, outs)
+    d = b.describe()
+    assert any(l["items"] > l["chunk"] * l["grid"] for l in d["launches"]), d
+    for _ in range(3):
+        for o in outs:
+            o.fill_(-1)
+        b()
+        torch.cuda.synchronize()
+        _check(outs, host)
+
+
 def test_batch_matches_single_launches():
     import torch
     ns = [22, 9, 17, 20]
