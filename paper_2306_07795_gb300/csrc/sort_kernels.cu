@@ -62,39 +62,49 @@ __device__ __forceinline__ bool keep(V a, V b)
     else return dev::keep_pair64<KEY>((uint64_t)a, (uint64_t)b);
 }
 
+// The register sets of a thread: NR independent rounds of 2^kSortRegBits
+// keys each, compared in the same stages (their orientation is the same:
+// it depends on the register index and the block only), so that the
+// compare-exchanges of one set fill the latency of the other's.
+template <typename V, int NR>
+using RegSets = V[NR][1 << kSortRegBits];
+
 // One stage on the registers, compact form: the pairs (j, j + 2^I); bit j
 // of `low` tells whether register j is the pair's low position.  Six
 // instructions per pair.
-template <int I, int KEY, typename V>
-__device__ __forceinline__ void ce_regs(V (&v)[1 << kSortRegBits], uint32_t low)
+template <int I, int KEY, int NR, typename V>
+__device__ __forceinline__ void ce_regs(RegSets<V, NR> &v, uint32_t low)
 {
 #pragma unroll
     for (int j = 0; j < (1 << kSortRegBits); ++j) {
         if (j & (1 << I)) continue;
         constexpr int bit = 1 << I;
-        const V a = v[j], b = v[j | bit];
         const bool lj = (low >> j) & 1u;
-        const bool k = lj ? keep<KEY>(a, b) : keep<KEY>(b, a);
-        v[j] = k ? a : b;
-        v[j | bit] = k ? b : a;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const V a = v[r][j], b = v[r][j | bit];
+            const bool k = lj ? keep<KEY>(a, b) : keep<KEY>(b, a);
+            v[r][j] = k ? a : b;
+            v[r][j | bit] = k ? b : a;
+        }
     }
 }
 
-template <int KEY, typename V>
-__device__ __forceinline__ void ce_regs_k(int k, V (&v)[1 << kSortRegBits], uint32_t low)
+template <int KEY, int NR, typename V>
+__device__ __forceinline__ void ce_regs_k(int k, RegSets<V, NR> &v, uint32_t low)
 {
-    if (k == 0) ce_regs<0, KEY>(v, low);
-    else if (k == 1) ce_regs<1, KEY>(v, low);
-    else if (k == 2) ce_regs<2, KEY>(v, low);
-    else ce_regs<3, KEY>(v, low);
+    if (k == 0) ce_regs<0, KEY, NR>(v, low);
+    else if (k == 1) ce_regs<1, KEY, NR>(v, low);
+    else if (k == 2) ce_regs<2, KEY, NR>(v, low);
+    else ce_regs<3, KEY, NR>(v, low);
 }
 
 // One stage on the registers with its orientation fixed at compile time:
 // the pairs (j, j + 2^K), and register j is the pair's low position (it
 // keeps the smaller key, Sec. 6.1) iff parity(j & HM) == B.  Three
 // instructions per pair: one comparison, two selects.
-template <int K, int HM, int B, int KEY, typename V>
-__device__ __forceinline__ void ce_fixed(V (&v)[1 << kSortRegBits])
+template <int K, int HM, int B, int KEY, int NR, typename V>
+__device__ __forceinline__ void ce_fixed(RegSets<V, NR> &v)
 {
 #pragma unroll
     for (int j = 0; j < (1 << kSortRegBits); ++j) {
@@ -102,45 +112,48 @@ __device__ __forceinline__ void ce_fixed(V (&v)[1 << kSortRegBits])
         const int jj = j | (1 << K);
         const bool low = (__popc(j & HM) & 1) == B;
         const int lo = low ? j : jj, hi = low ? jj : j;
-        const V a = v[lo], b = v[hi];
-        const bool k = keep<KEY>(a, b);
-        v[lo] = k ? a : b;
-        v[hi] = k ? b : a;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const V a = v[r][lo], b = v[r][hi];
+            const bool k = keep<KEY>(a, b);
+            v[r][lo] = k ? a : b;
+            v[r][hi] = k ? b : a;
+        }
     }
 }
 
 // Select the variant of stage bit K for the block's (hm, b): hm has bit K
 // clear; both are the same for every thread of the block.
-template <int K, int KEY, int HM, typename V>
-__device__ __forceinline__ void ce_dispatch(V (&v)[1 << kSortRegBits], uint32_t hm, uint32_t b)
+template <int K, int KEY, int HM, int NR, typename V>
+__device__ __forceinline__ void ce_dispatch(RegSets<V, NR> &v, uint32_t hm, uint32_t b)
 {
     if constexpr (HM < (1 << kSortRegBits)) {
         if constexpr ((HM >> K) & 1) {
-            ce_dispatch<K, KEY, HM + 1>(v, hm, b);
+            ce_dispatch<K, KEY, HM + 1, NR>(v, hm, b);
         } else {
             if (hm == (uint32_t)HM) {
-                if (b) ce_fixed<K, HM, 1, KEY>(v);
-                else ce_fixed<K, HM, 0, KEY>(v);
+                if (b) ce_fixed<K, HM, 1, KEY, NR>(v);
+                else ce_fixed<K, HM, 0, KEY, NR>(v);
             } else {
-                ce_dispatch<K, KEY, HM + 1>(v, hm, b);
+                ce_dispatch<K, KEY, HM + 1, NR>(v, hm, b);
             }
         }
     }
 }
 
 // The stage in register bit k (known at compile time after unrolling).
-template <int KEY, typename V>
-__device__ __forceinline__ void ce_stage(int k, V (&v)[1 << kSortRegBits], uint32_t hm,
-                                         uint32_t b)
+template <int KEY, int NR, typename V>
+__device__ __forceinline__ void ce_stage(int k, RegSets<V, NR> &v, uint32_t hm, uint32_t b)
 {
     static_assert(kSortRegBits == 4, "one case per register bit");
-    if (k == 0) ce_dispatch<0, KEY, 0>(v, hm, b);
-    else if (k == 1) ce_dispatch<1, KEY, 0>(v, hm, b);
-    else if (k == 2) ce_dispatch<2, KEY, 0>(v, hm, b);
-    else ce_dispatch<3, KEY, 0>(v, hm, b);
+    if (k == 0) ce_dispatch<0, KEY, 0, NR>(v, hm, b);
+    else if (k == 1) ce_dispatch<1, KEY, 0, NR>(v, hm, b);
+    else if (k == 2) ce_dispatch<2, KEY, 0, NR>(v, hm, b);
+    else ce_dispatch<3, KEY, 0, NR>(v, hm, b);
 }
 
-template <int E_LOG, int KEY, bool UNROLLED>
+// NR rounds at a time (NR = 2 needs at least two rounds per group).
+template <int E_LOG, int KEY, bool UNROLLED, int NR>
 __device__ __forceinline__ void run_groups(const SortDesc &sd, uint32_t sbase, uint64_t bc)
 {
     using V = typename KeyWord<E_LOG>::type;
@@ -167,14 +180,21 @@ __device__ __forceinline__ void run_groups(const SortDesc &sd, uint32_t sbase, u
         }
         const uint32_t rounds = 1u << sd.round_bits;
         const uint32_t end = (uint32_t)G.first + G.count;
-        for (uint32_t rd = 0; rd < rounds; ++rd) {
-            uint32_t qb = tq;
-            for (uint32_t t = 0; t < sd.round_bits; ++t)
-                if ((rd >> t) & 1u) qb ^= G.round[t];
-            const uint32_t qbyte = qb << E_LOG;
-            V v[E];
+        for (uint32_t rd = 0; rd < rounds; rd += NR) {
+            uint32_t qbyte[NR];
 #pragma unroll
-            for (int j = 0; j < E; ++j) v[j] = lds_key<E_LOG>(sbase + (qbyte ^ roff[j]));
+            for (int r = 0; r < NR; ++r) {
+                uint32_t qb = tq;
+                for (uint32_t t = 0; t < sd.round_bits; ++t)
+                    if (((rd + (uint32_t)r) >> t) & 1u) qb ^= G.round[t];
+                qbyte[r] = qb << E_LOG;
+            }
+            V v[NR][E];
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    v[r][j] = lds_key<E_LOG>(sbase + (qbyte[r] ^ roff[j]));
             // stage first + k pairs the registers that differ in bit k; its
             // orientation is the block's (hmask, bit of bc)
 #pragma unroll
@@ -184,15 +204,18 @@ __device__ __forceinline__ void run_groups(const SortDesc &sd, uint32_t sbase, u
                     const SortStage &st = sd.st[s];
                     const uint32_t blk = (uint32_t)(bc >> s) & 1u;
                     if constexpr (UNROLLED) {
-                        ce_stage<KEY>(k, v, st.hmask, blk);
+                        ce_stage<KEY, NR>(k, v, st.hmask, blk);
                     } else {
                         const uint32_t low0 = st.low0;
-                        ce_regs_k<KEY>(k, v, blk ? ~low0 : low0);
+                        ce_regs_k<KEY, NR>(k, v, blk ? ~low0 : low0);
                     }
                 }
             }
 #pragma unroll
-            for (int j = 0; j < E; ++j) sts_key<E_LOG>(sbase + (qbyte ^ roff[j]), v[j]);
+            for (int r = 0; r < NR; ++r)
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    sts_key<E_LOG>(sbase + (qbyte[r] ^ roff[j]), v[r][j]);
         }
         __syncthreads();
     }
@@ -224,8 +247,12 @@ __device__ __forceinline__ uint64_t block_stage_bits(const PassDesc &d, const So
     return ((uint64_t)hi << 32) | lo;
 }
 
-template <int E_LOG, int KEY, bool UNROLLED>
-__global__ void __launch_bounds__(256)
+// Registers capped for 4 resident blocks with 4-byte keys and one register
+// set (64 per thread: small tiles allow more blocks than 3) and for 3
+// otherwise (80 per thread for 8-byte keys, or for two sets of 4-byte keys,
+// which run on 64 KiB tiles only).
+template <int E_LOG, int KEY, bool UNROLLED, int NR>
+__global__ void __launch_bounds__(256, (E_LOG == 2 && NR == 1) ? 4 : 3)
     bmmc_sort_pass(const __grid_constant__ PassDesc d, const __grid_constant__ SortDesc sd,
                    const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
@@ -242,7 +269,7 @@ __global__ void __launch_bounds__(256)
     dev::cp_async_wait_all();
     __syncthreads();
     const uint64_t bc = block_stage_bits(d, *tab, cta);
-    run_groups<E_LOG, KEY, UNROLLED>(*tab, sbase, bc);
+    run_groups<E_LOG, KEY, UNROLLED, NR>(*tab, sbase, bc);
     dev::tile_store<E_LOG, dev::kKeyNone>(d, a, out, sbase);
 }
 
@@ -305,9 +332,9 @@ cudaError_t launch_pdl(void (*kernel)(Args...), dim3 grid, dim3 block, size_t sm
 constexpr int kMaxDevices = 64;
 constexpr int kSortTile = 64 * 1024;  // largest tile buffer of a fused pass
 constexpr int kSortSmem = kSortTile + (int)((sizeof(SortDesc) + 127) & ~(size_t)127);
-std::atomic<bool> g_sort_attr[kMaxDevices][2][7][2];
+std::atomic<bool> g_sort_attr[kMaxDevices][2][7][2][2];
 
-template <int E_LOG, int KEY, bool UNROLLED>
+template <int E_LOG, int KEY, bool UNROLLED, int NR>
 cudaError_t launch_variant(const PassDesc &d, const SortDesc &sd, const void *in, void *out,
                            cudaStream_t s)
 {
@@ -315,24 +342,40 @@ cudaError_t launch_variant(const PassDesc &d, const SortDesc &sd, const void *in
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::atomic<bool> &flag = g_sort_attr[dev][E_LOG - 2][KEY][UNROLLED ? 1 : 0];
+    std::atomic<bool> &flag = g_sort_attr[dev][E_LOG - 2][KEY][UNROLLED ? 1 : 0][NR - 1];
     if (!flag.load(std::memory_order_acquire)) {
-        err = cudaFuncSetAttribute(bmmc_sort_pass<E_LOG, KEY, UNROLLED>,
+        err = cudaFuncSetAttribute(bmmc_sort_pass<E_LOG, KEY, UNROLLED, NR>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
         if (err != cudaSuccess) return err;
         flag.store(true, std::memory_order_release);
     }
-    return launch_pdl(bmmc_sort_pass<E_LOG, KEY, UNROLLED>, dim3(1u << d.n_cta), dim3(256),
+    return launch_pdl(bmmc_sort_pass<E_LOG, KEY, UNROLLED, NR>, dim3(1u << d.n_cta), dim3(256),
                       d.smem_bytes + sizeof(SortDesc), s, d, sd, static_cast<const uint8_t *>(in),
                       static_cast<uint8_t *>(out));
+}
+
+// 4-byte keys on 64 KiB tiles (four rounds per group): two rounds at a time.
+// Shared memory already holds only 3 such blocks per SM, so the 80
+// registers of two sets cost no resident block; on 32 KiB tiles they would
+// (measured on GB300, n = 22: 0.50 ms against 0.42 with one set; n = 24:
+// 1.50 against 1.56).  The 32 keys of 8-byte ones would not fit the
+// registers.
+template <int E_LOG, int KEY, bool UNROLLED>
+cudaError_t launch_rounds(const PassDesc &d, const SortDesc &sd, const void *in, void *out,
+                          cudaStream_t s)
+{
+    if constexpr (E_LOG == 2) {
+        if (sd.round_bits >= 2) return launch_variant<E_LOG, KEY, UNROLLED, 2>(d, sd, in, out, s);
+    }
+    return launch_variant<E_LOG, KEY, UNROLLED, 1>(d, sd, in, out, s);
 }
 
 template <int E_LOG, int KEY>
 cudaError_t launch_typed(const PassDesc &d, const SortDesc &sd, const void *in, void *out,
                          cudaStream_t s)
 {
-    return sd.unrolled ? launch_variant<E_LOG, KEY, true>(d, sd, in, out, s)
-                       : launch_variant<E_LOG, KEY, false>(d, sd, in, out, s);
+    return sd.unrolled ? launch_rounds<E_LOG, KEY, true>(d, sd, in, out, s)
+                       : launch_rounds<E_LOG, KEY, false>(d, sd, in, out, s);
 }
 
 }  // namespace

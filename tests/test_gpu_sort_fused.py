@@ -93,7 +93,8 @@ def test_fused_equals_oracle_network(name):
 
 @pytest.mark.parametrize("n,name,block_log2", [(18, "float32", 0), (20, "float32", 0),
                                                (20, "float64", 0), (19, "int32", 14),
-                                               (17, "uint64", 15)])
+                                               (17, "uint64", 15), (16, "int32", 16),
+                                               (19, "uint32", 16), (20, "float32", 16)])
 def test_fused_equals_host_emulation(n, name, block_log2):
     """The kernels index shared memory and registers exactly as the host walk
     of the same tables does (bmmc_sort_plan_emulate)."""
