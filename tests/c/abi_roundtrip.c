@@ -1,7 +1,7 @@
 /*
  * abi_roundtrip.c -- a C program that uses the library through its C ABI
  * only (include/bmmc.h, libbmmc.so and the CUDA runtime), with no Python in
- * the process.  Test infrastructure: tests/test_gpu_c_abi.py builds it, feeds
+ * the process.  Test infrastructure: tests/test_c_abi.py builds it, feeds
  * it an array and compares what it writes with the oracle.
  *
  * usage: abi_roundtrip n elem_bytes c row_0 ... row_{n-1} < in.bin > out.bin

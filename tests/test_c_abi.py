@@ -27,12 +27,15 @@ def _nvcc():
     pytest.skip("nvcc not found")
 
 
-def _build(tmp_path):
+EXTRAS = os.path.join(ROOT, "tests", "c", "abi_extras.c")
+
+
+def _build(tmp_path, src=SRC):
     import paper_2306_07795_gb300 as bm
     bm.lib()  # builds libbmmc.so if needed
-    exe = str(tmp_path / "abi_roundtrip")
+    exe = str(tmp_path / os.path.splitext(os.path.basename(src))[0])
     cmd = [_nvcc(), "-O2", "-I", os.path.join(ROOT, "include"),
-           SRC, "-L", LIBDIR, "-lbmmc", "-Xlinker", "-rpath," + LIBDIR, "-o", exe]
+           src, "-L", LIBDIR, "-lbmmc", "-Xlinker", "-rpath," + LIBDIR, "-o", exe]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     return exe
@@ -40,6 +43,81 @@ def _build(tmp_path):
 
 def test_c_program_builds(tmp_path):
     assert os.path.exists(_build(tmp_path))
+
+
+def test_c_extras_program_builds(tmp_path):
+    assert os.path.exists(_build(tmp_path, EXTRAS))
+
+
+def _job(arrays, payloads=True):
+    """The job abi_extras.c reads: headers as uint64 words, then bytes."""
+    words = [len(arrays)]
+    for n, e, rows, c, _ in arrays:
+        words += [n, e, c] + [int(r) for r in rows]
+    data = np.array(words, dtype=np.uint64).tobytes()
+    if payloads:
+        for *_, arr in arrays:
+            data += np.ascontiguousarray(arr).reshape(-1).view(np.uint8).tobytes()
+    return data
+
+
+def _run_extras(tmp_path, mode, job):
+    r = subprocess.run([_build(tmp_path, EXTRAS), mode], input=job, capture_output=True,
+                       timeout=300)
+    assert r.returncode == 0, (mode, r.returncode, r.stderr.decode())
+    return r.stdout
+
+
+def test_c_shard_plans(tmp_path):
+    """bmmc_shard.h from C (host only): one exchange between two local steps
+    for dense matrices, every index checked by bmmc_shard_plan_verify."""
+    arrays = []
+    for n in (6, 10, 14, 20):
+        rows, c = wl.dense_bmmc(n, 30 + n, _inv)
+        arrays.append((n, 4, rows, c, None))
+    out = np.frombuffer(_run_extras(tmp_path, "shard", _job(arrays, payloads=False)),
+                        dtype=np.uint64).reshape(-1, 2)
+    assert out.shape == (4, 2)
+    assert all(steps in (3, 5) for steps in out[:, 0]) and not out[:, 1].any(), out
+
+
+def _mixed_arrays():
+    arrays = []
+    for i, (n, e) in enumerate([(6, 4), (12, 8), (16, 16), (19, 4), (21, 8), (9, 4)]):
+        rows, c = wl.dense_bmmc(n, 50 + i, _inv) if i % 2 == 0 else (wl.random_bp(n, i), 0)
+        arrays.append((n, e, rows, c, wl.payload(n, e, seed=i)))
+    return arrays
+
+
+def _split(out, arrays):
+    pos = 0
+    for n, e, rows, c, arr in arrays:
+        size = (1 << n) * e
+        yield out[pos:pos + size], n, e, rows, c, arr
+        pos += size
+    assert pos == len(out)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["batch", "server"])
+def test_c_batch_and_server_match_oracle(tmp_path, mode):
+    arrays = _mixed_arrays()
+    out = _run_extras(tmp_path, mode, _job(arrays))
+    for got, n, e, rows, c, arr in _split(out, arrays):
+        want = np.ascontiguousarray(oracle.apply(n, rows, c, arr, elem_bytes=e))
+        assert got == want.reshape(-1).view(np.uint8).tobytes(), (mode, n, e)
+
+
+@pytest.mark.gpu
+def test_c_sort_matches_numpy(tmp_path):
+    g = wl.rng(12)
+    arrays = []
+    for n in (5, 12, 13, 17, 23):
+        keys = g.integers(-2**31, 2**31 - 1, size=1 << n, dtype=np.int64).astype(np.int32)
+        arrays.append((n, 4, [1 << i for i in range(n)], 0, keys))
+    out = _run_extras(tmp_path, "sort", _job(arrays))
+    for got, n, e, rows, c, keys in _split(out, arrays):
+        assert np.array_equal(np.frombuffer(got, dtype=np.int32), np.sort(keys)), n
 
 
 def _inv(rows):
