@@ -394,6 +394,7 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
     const int elem_units_log = e_log - 2;  // 4-byte words per element
     (void)elem_units_log;
     std::vector<int> free_bits;
+    free_bits.reserve(C > 3 ? C - 3 : 0);
     for (int b = 3; b < C; ++b) free_bits.push_back(b);
 
     struct Cand {
@@ -401,6 +402,7 @@ int derive_pass_span(const f2::Mat &t, uint64_t c, int n, int e_log,
         int rot_lane[2];  // lane bit feeding rotation bit 0 / 1, -1 = none
     };
     std::vector<Cand> cands;
+    cands.reserve(4 * (size_t)C * (size_t)C + 4);  // every pair of free bits, 4 variants
     auto add_rot_variants = [&](int l3, int l4) {
         cands.push_back({l3, l4, {-1, -1}});
         if (w_log >= 1) {
