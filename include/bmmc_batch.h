@@ -34,7 +34,7 @@ typedef struct bmmc_batch_s *bmmc_batch;
 size_t bmmc_batch_workspace_bytes(const bmmc_plan *plans, int count);
 
 /* Device bytes of a batch's tables (bmmc_batch_create's `table`): about
- * 1.8 KB per pass plus 32 bytes per pass, plus 96 bytes of counters.  0 for
+ * 1.4 KB per pass plus 32 bytes per pass, plus 96 bytes of counters.  0 for
  * invalid arguments. */
 size_t bmmc_batch_table_bytes(const bmmc_plan *plans, int count);
 
