@@ -1,5 +1,6 @@
-"""Seeded random combinations of size, element size, matrix class, strategy
-and tile options, each checked element by element against the oracle.  The
+"""Seeded random combinations of size, element size, matrix class, strategy,
+tile options and tile-load instruction, each checked element by element
+against the oracle.  The
 systematic tests cover each option on its own; this one covers them mixed."""
 
 import numpy as np
@@ -47,6 +48,8 @@ def test_random_combinations():
     checked = 0
     for _ in range(240):
         n, e, kind, rows, c, flags, seg, tile, order = _case(g)
+        if g.random() < 0.3:  # tile loads by tensor copies where the plan allows
+            flags |= bm.BMMC_PLAN_TMA_LOAD
         try:
             p = bm.Plan(n, rows, c, e, flags=flags, seg_bits=seg, cta_tile_log2=tile,
                         tile_order=order)
