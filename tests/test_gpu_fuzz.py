@@ -1,7 +1,7 @@
 """Seeded random combinations of size, element size, matrix class, strategy,
 tile options and tile-load instruction, each checked element by element
-against the oracle.  The
-systematic tests cover each option on its own; this one covers them mixed."""
+against the oracle.  The systematic tests cover each option on its own; this
+one covers them mixed."""
 
 import numpy as np
 import pytest
