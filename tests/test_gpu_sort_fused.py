@@ -116,6 +116,49 @@ def test_fused_equals_host_emulation(n, name, block_log2):
     assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
 
 
+def test_fused_random_options():
+    """Seeded random sizes, row counts, key types, block sizes and compare
+    forms: the kernels equal the host emulation of the same plan bit for bit
+    (float keys with NaN payloads, infinities and both zeros), and integer
+    keys equal numpy's sort row by row."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(77))
+    names = list(DT)
+    checked = 0
+    for it in range(48):
+        name = names[it % len(names)]
+        np_dtype, key = DT[name]
+        n = int(g.integers(1, 19))
+        b = int(g.integers(0, 3))
+        block_log2 = int(g.choice([0, 14, 15, 16]))
+        compare_code = int(g.choice([0, 1, 2]))
+        try:
+            h = B.bmmc_sort_plan_create(n, b, key, block_log2, compare_code)
+        except B.BmmcError as err:
+            assert err.code == B.BMMC_ERR_UNSUPPORTED, (n, b, name, block_log2)
+            continue
+        arr = _keys(np_dtype, 1 << (n + b), 1000 + it)
+        want = np.empty_like(arr)
+        B.bmmc_sort_plan_emulate(h, ctypes.c_void_p(arr.ctypes.data),
+                                 ctypes.c_void_p(want.ctypes.data))
+        x = _to_torch(arr)
+        y = torch.full_like(x, -1)
+        ws = torch.empty(max(16, B.bmmc_sort_workspace_bytes(h)), dtype=torch.uint8,
+                         device="cuda")
+        B.bmmc_sort_execute(h, x.data_ptr(), y.data_ptr(), ws.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        B.bmmc_sort_plan_destroy(h)
+        got = y.cpu().numpy().view(np_dtype)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), \
+            (it, n, b, name, block_log2, compare_code)
+        if not np.issubdtype(np_dtype, np.floating):
+            assert np.array_equal(got.reshape(1 << b, -1),
+                                  np.sort(arr.reshape(1 << b, -1), axis=1)), (it, n, b, name)
+        checked += 1
+    assert checked >= 30
+
+
 @pytest.mark.parametrize("n", [20, 24])
 def test_fused_matches_torch_sort(n):
     import torch
